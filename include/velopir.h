@@ -1,0 +1,223 @@
+/*
+ * velopir.h -- C ABI of libvelopir.so: batched TFHE gate bootstrapping on one
+ * GB300 (sm_103a) and the server-side circuits of VeLoPIR's three query modes.
+ *
+ * Paper: "Versatile and Fast Location-Based PIR with FHE over the Torus"
+ * (VeLoPIR).  Section 2.2 defines TLWE encryption, Ecd, Dec and the gate
+ * HomAND = Bootstrap((0,-1/8) + ct1 + ct2); Bootstrap = BlindRotate,
+ * SampleExtract, KeySwitch with internals from tfhe-2 (Chillotti et al.,
+ * J. Cryptol. 2020); parameters from the Appendix table (n = 630, N = 1024,
+ * k = 1, l = 3, Bg = 2^7, key-switch base 2^2 with t = 8 levels).
+ *
+ * Conventions shared by every entry point:
+ *  - Torus values are uint32_t with 1.0 == 2^32; all arithmetic is mod 2^32.
+ *  - An LWE ciphertext is 631 contiguous uint32_t: a[0..629] then b.
+ *  - A multi-bit value is an array of bit ciphertexts, least significant bit
+ *    first (ct[i] encrypts bit i).
+ *  - Every function returns 0 (VELOPIR_OK) or a negative VELOPIR_ERR_* code;
+ *    velopir_last_error() then describes the failure.  No function aborts.
+ *  - Buffers belong to the caller.  A pointer may be host or device memory
+ *    (classified with cudaPointerGetAttributes); results are written to the
+ *    memory kind the caller passed.  Host buffers are staged through device
+ *    scratch owned by the context.
+ *  - Calls on one context are serialised on the context's CUDA stream and are
+ *    synchronous unless stated otherwise (velopir_submit is asynchronous).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef VELOPIR_H
+#define VELOPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VELOPIR_LWE_N 630     /* LWE dimension n (Appendix parameter table) */
+#define VELOPIR_RING_N 1024   /* polynomial size N (Appendix parameter table) */
+#define VELOPIR_LWE_WORDS 631 /* n mask words + b */
+
+enum {
+    VELOPIR_OK = 0,
+    VELOPIR_ERR_ARG = -1,     /* null pointer, bad size, unknown gate, bad params */
+    VELOPIR_ERR_NOKEY = -2,   /* no cloud key loaded on this context */
+    VELOPIR_ERR_OOM = -3,     /* request exceeds the HBM budget or cudaMalloc failed */
+    VELOPIR_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed */
+    VELOPIR_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    VELOPIR_ERR_BUSY = -6,    /* serving queue full / ticket not finished */
+    VELOPIR_ERR_NOCUDA = -7   /* no CUDA device is visible */
+};
+
+/* Gates (Section 2.2 names HomAND, HomXOR, HomXNOR; the others are tfhe-2's
+ * gate set under the same encoding).  Each binary gate is one bootstrap of a
+ * linear pre-combination; MUX(c, a, b) = c ? a : b uses two blind rotations
+ * and one key switch. */
+typedef enum {
+    VP_AND = 0, VP_NAND, VP_OR, VP_NOR, VP_XOR, VP_XNOR,
+    VP_ANDNY, /* (NOT c1) AND c2 */
+    VP_ANDYN, /* c1 AND (NOT c2) */
+    VP_ORNY,  /* (NOT c1) OR c2  */
+    VP_ORYN,  /* c1 OR (NOT c2)  */
+    VP_MUX
+} velopir_gate;
+
+/* Implementation of the external product inside blind rotation.  Every path
+ * returns bit-identical ciphertexts; they differ only in speed. */
+typedef enum {
+    VP_PATH_INT32_DENSE = 0, /* dense negacyclic contraction on the integer pipe */
+    VP_PATH_NTT = 1,         /* exact two-prime number-theoretic transform (default) */
+    VP_PATH_TENSOR_F16 = 2   /* exact small-integer limbs on tcgen05 kind::f16 */
+} velopir_path;
+
+typedef struct {
+    int32_t n, N, k, l, bg_bits, ks_t, ks_base_bits; /* must be 630,1024,1,3,7,8,2 */
+} velopir_params;
+
+typedef struct velopir_ctx velopir_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may allocate (keys + scratch); 0 = no cap.  cuda_stream
+ * (a cudaStream_t, nullable) is the stream every launch goes to; NULL makes
+ * the context create and own a non-blocking stream.  *out is set to NULL on
+ * failure.  Errors: ERR_ARG, ERR_NOCUDA, ERR_CUDA. */
+int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Release every device allocation of the context and the context itself.
+ * Waits for outstanding work first.  NULL is accepted. */
+int velopir_destroy(velopir_ctx *ctx);
+
+/* Upload the cloud key (Section 2.2 KeyGen's evaluation key evk).
+ *   bk : bootstrapping key, uint32_t[630][6][2][1024]; entry [i][r][j] is
+ *        component j (0 = a(X), 1 = b(X)) of TRGSW row r = 2(p-1)+q of
+ *        BK_i = TRGSW_K(s_i) (level p = 1..3, component q), coefficients
+ *        in increasing degree.  bk_words must be 630*6*2*1024.
+ *   ksk: key-switching key, uint32_t[1024][8][4][631]; entry [i][j][v] is
+ *        LWE_s(v * K_i * 2^(32-2(j+1))).  ksk_words must be 1024*8*4*631.
+ * The library keeps device copies in its own layout (padded KSK rows, the
+ * transformed BK of the selected path).  Replaces a previously loaded key.
+ * Errors: ERR_ARG (params not the paper's set, wrong sizes), ERR_OOM, ERR_CUDA. */
+int velopir_load_cloud_key(velopir_ctx *ctx, const velopir_params *params,
+                           const uint32_t *bk, size_t bk_words,
+                           const uint32_t *ksk, size_t ksk_words);
+
+/* Select the external-product implementation (default VP_PATH_NTT).  The key
+ * stays loaded: the path's transformed copy of BK is built on the device the
+ * first time the path runs.  Errors: ERR_ARG (unknown or unavailable path). */
+int velopir_set_path(velopir_ctx *ctx, velopir_path path);
+
+/* One gate on each of `count` independent inputs, all bootstraps issued as
+ * one batch (blind rotation of every input shares each step's BK_i).
+ *   lwe_in : uint32_t[count][arity][631], arity 2 (3 for VP_MUX: c, a, b)
+ *   lwe_out: uint32_t[count][631]
+ * count == 0 is a no-op.  Errors: ERR_ARG, ERR_NOKEY, ERR_OOM, ERR_CUDA,
+ * ERR_TIMEOUT. */
+int velopir_bootstrap_batch(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,
+                            uint32_t *lwe_out, size_t count);
+
+/* The same gates issued one bootstrap per kernel launch (no batching): the
+ * "plain" baseline against which batching is measured.  Same arguments. */
+int velopir_bootstrap_plain(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,
+                            uint32_t *lwe_out, size_t count);
+
+/* IntV (Alg. InterValid) against a plaintext database of D rectangles.
+ *   enc_x, enc_y: uint32_t[32][631] each, bitwise encryptions of unsigned
+ *                 32-bit coordinates x and y.
+ *   rects       : uint32_t[D][4] = x_lo, x_hi, y_lo, y_hi (plaintext, unsigned)
+ *   out_bits    : uint32_t[D][631]; entry d encrypts
+ *                 x_lo <= x < x_hi AND y_lo <= y < y_hi (half-open, Theorem bb1).
+ * Comparators follow Alg. HomCompLeOPT with XNOR/MUX against plaintext bits
+ * rewritten into single gates and the top bit flipped for unsigned order;
+ * 131 bootstraps per entry issued as 34 batched layers.
+ * Errors: ERR_ARG, ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
+int velopir_interval_query(velopir_ctx *ctx, const uint32_t *enc_x, const uint32_t *enc_y,
+                           const uint32_t *rects, size_t D, uint32_t *out_bits);
+
+/* CoV (Alg. CoV with Alg. HomEqOPT) against D plaintext grid cells.
+ *   enc_cell: uint32_t[32][631]: bits 0..15 encrypt x, bits 16..31 encrypt y.
+ *   cells   : uint32_t[D], packed (y << 16) | x.
+ *   out_bits: uint32_t[D][631]; entry d encrypts (x, y) == cell d.
+ * 31 bootstraps per entry in 5 batched layers.  Errors as above. */
+int velopir_coordinate_query(velopir_ctx *ctx, const uint32_t *enc_cell, const uint32_t *cells,
+                             size_t D, uint32_t *out_bits);
+
+/* IdM: Alg. HomEqOPT of an encrypted identifier against D plaintext ids.
+ *   enc_id : uint32_t[id_bits][631], 1 <= id_bits <= 32.
+ *   ids    : uint32_t[D] (only the low id_bits bits are compared).
+ *   payload: NULL, or uint32_t[D] plaintext payloads.
+ *   out    : payload == NULL: uint32_t[D][631] match bits.
+ *            payload != NULL: uint32_t[payload_bits][631], the HomSum of the
+ *            zeroed-out payloads (Alg. HomBitwiseAND with a plaintext
+ *            payload, then the pairwise XOR reduction of Section 5), i.e. an
+ *            encryption of the payload of the matching entry (0 if none).
+ *   1 <= payload_bits <= 32.  Errors as above. */
+int velopir_id_match(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, const uint32_t *ids,
+                     size_t D, const uint32_t *payload, int payload_bits, uint32_t *out);
+
+/* ---- serving: asynchronous queries with continuous batching ------------- */
+
+typedef enum { VP_QUERY_INTV = 0, VP_QUERY_COV = 1, VP_QUERY_IDM = 2 } velopir_query_kind;
+
+typedef struct {
+    int32_t kind;            /* velopir_query_kind */
+    int32_t id_bits;         /* IdM only */
+    int32_t payload_bits;    /* IdM with payload only */
+    int32_t reserved;
+    const uint32_t *enc_a;   /* IntV: enc_x; CoV: enc_cell; IdM: enc_id (host or device) */
+    const uint32_t *enc_b;   /* IntV: enc_y; otherwise NULL */
+    const uint32_t *db;      /* rects / cells / ids (host memory) */
+    const uint32_t *payload; /* IdM payloads (host memory) or NULL */
+    size_t D;
+    uint32_t *out;           /* result buffer, same shapes as the synchronous calls */
+} velopir_query;
+
+/* Enqueue a query.  It is admitted into the running batch as soon as the
+ * context's HBM budget allows; its gate layers are merged with those of every
+ * other admitted query into shared launches.  *ticket identifies it.  The
+ * caller must not touch enc_*, db, payload or out until velopir_poll reports
+ * done.  Errors: ERR_ARG, ERR_NOKEY, ERR_BUSY (queue full). */
+int velopir_submit(velopir_ctx *ctx, const velopir_query *q, uint64_t *ticket);
+
+/* Advance the serving loop by at most one merged layer launch and report
+ * whether `ticket` has finished (*done = 1; its result is in q->out).
+ * Errors: ERR_ARG (unknown ticket), ERR_CUDA, ERR_TIMEOUT. */
+int velopir_poll(velopir_ctx *ctx, uint64_t ticket, int *done);
+
+/* Number of admitted and waiting queries.  Errors: ERR_ARG. */
+int velopir_queue_depth(velopir_ctx *ctx, size_t *admitted, size_t *waiting);
+
+/* Wait for all work on the context's stream.  Errors: ERR_CUDA, ERR_TIMEOUT. */
+int velopir_sync(velopir_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  NULL ctx gives
+ * the last failure of velopir_create on this thread. */
+const char *velopir_last_error(velopir_ctx *ctx);
+
+/* Kernel launches this context has issued since creation (for launch counting). */
+uint64_t velopir_launch_count(velopir_ctx *ctx);
+
+/* ---- client side (host only; no GPU involved) --------------------------- */
+/* Key generation and encryption from caller-supplied random numbers (masks,
+ * noise integers, key bits), so that any seeded generator can drive them.   */
+
+/* BK and KSK from: s[630] and K[1024] key bits (0/1), bk_a/bk_e
+ * uint32_t[630][6][1024] masks and noise, ksk_a uint32_t[1024][8][4][630],
+ * ksk_e uint32_t[1024][8][4].  Outputs in the layouts velopir_load_cloud_key
+ * takes.  Errors: ERR_ARG. */
+int velopir_client_keygen(const velopir_params *params, const uint32_t *s, const uint32_t *K,
+                          const uint32_t *bk_a, const uint32_t *bk_e,
+                          const uint32_t *ksk_a, const uint32_t *ksk_e,
+                          uint32_t *bk_out, uint32_t *ksk_out);
+
+/* Encrypt `count` bits (Section 2.2 Enc with Ecd): ct_i = (a_i, <a_i,s> + Ecd(bit_i) + e_i).
+ * a: uint32_t[count][630], e: uint32_t[count], out: uint32_t[count][631]. */
+int velopir_client_encrypt_bits(const uint32_t *s, const uint32_t *bits, const uint32_t *a,
+                                const uint32_t *e, size_t count, uint32_t *out);
+
+/* Decrypt `count` ciphertexts (Section 2.2 Dec): bit = phase in [0, 1/2). */
+int velopir_client_decrypt_bits(const uint32_t *s, const uint32_t *ct, size_t count, uint32_t *bits_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VELOPIR_H */

@@ -1,0 +1,790 @@
+// C ABI of libvelopir.so (declared in include/velopir.h): context, key upload,
+// layer-batched execution of gate programs, the three VeLoPIR query modes and
+// the continuous-batching serving loop.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/velopir.h"
+#include "sched.h"
+#include "vp_internal.h"
+
+using namespace vp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ServeQuery;
+
+}  // namespace
+
+struct velopir_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;      // 0 = unlimited
+    size_t allocated = 0;   // bytes currently held
+    std::string err;
+    uint64_t launches = 0;
+    int path = VP_PATH_INT32_DENSE;
+    int big_rows = 1 << 16; // scratch capacity in extracted rows
+
+    bool key_loaded = false;
+    DevBuf bk, ksk, bk_ntt, big, jobs_br, jobs_ks, jobs_fr, pool, in, out, errw;
+    bool bk_ntt_ready = false;
+
+    std::deque<std::unique_ptr<ServeQuery>> waiting;
+    std::vector<std::unique_ptr<ServeQuery>> active;
+    std::vector<std::unique_ptr<ServeQuery>> finished;
+    uint64_t next_ticket = 1;
+    size_t serve_reserved = 0;
+    DevBuf s_br, s_ks, s_fr;   // serving-step job buffers
+};
+
+namespace {
+
+int fail(velopir_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(c, VELOPIR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void dev_free(velopir_ctx *c, DevBuf &b)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        c->allocated -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Grow-only device buffer, accounted against the HBM budget.
+int ensure(velopir_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.bytes) return VELOPIR_OK;
+    bytes = std::max(bytes, b.bytes + b.bytes / 2);
+    if (c->budget && c->allocated - b.bytes + bytes > c->budget)
+        return fail(c, VELOPIR_ERR_OOM, "HBM budget of %zu bytes exceeded (need %zu more)", c->budget,
+                    bytes - b.bytes);
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, b);
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VELOPIR_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    b.p = p;
+    b.bytes = bytes;
+    c->allocated += bytes;
+    return VELOPIR_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T> T *as(const DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+uint32_t *resolve(uint64_t v, uint32_t *pool, const std::vector<int> &phys)
+{
+    if (!(v & kSlotTag)) return reinterpret_cast<uint32_t *>(v);
+    return pool + (size_t)phys[(size_t)(v & ~kSlotTag)] * kSlotWords;
+}
+
+struct Launch {
+    int kind;   // 0 = blind rotation, 1 = key switch, 2 = free gates
+    size_t off;
+    int n;
+};
+
+struct Flat {
+    std::vector<BrJob> br;
+    std::vector<KsJob> ks;
+    std::vector<FreeJob> fr;
+    std::vector<Launch> launches;
+};
+
+// Append one layer's jobs, split into chunks whose blind rotations fit the
+// extracted-row scratch; pointers are resolved against `pool`.
+void flatten_layer(const Layer &L, int cap, uint32_t *pool, const std::vector<int> &phys, Flat &F)
+{
+    const size_t nks = L.ks.size();
+    size_t g = 0;
+    while (g < nks) {
+        const int br0 = L.ks[g].e0;
+        size_t g1 = g;
+        int br1 = br0;
+        while (g1 < nks) {
+            const int hi = std::max(L.ks[g1].e0, L.ks[g1].e1) + 1;
+            if (hi - br0 > cap && g1 > g) break;
+            br1 = std::max(br1, hi);
+            ++g1;
+        }
+        const size_t bo = F.br.size();
+        for (int b = br0; b < br1; ++b) {
+            BrJob j = L.br[b];
+            j.in0 = j.in0 ? resolve((uint64_t)(uintptr_t)j.in0, pool, phys) : nullptr;
+            j.in1 = j.in1 ? resolve((uint64_t)(uintptr_t)j.in1, pool, phys) : nullptr;
+            j.big = b - br0;
+            F.br.push_back(j);
+        }
+        F.launches.push_back({0, bo, br1 - br0});
+        const size_t ko = F.ks.size();
+        for (size_t q = g; q < g1; ++q) {
+            KsJob k = L.ks[q];
+            k.e0 -= br0;
+            if (k.e1 >= 0) k.e1 -= br0;
+            k.out = resolve((uint64_t)(uintptr_t)k.out, pool, phys);
+            F.ks.push_back(k);
+        }
+        F.launches.push_back({1, ko, (int)(g1 - g)});
+        g = g1;
+    }
+}
+
+void flatten_free(const std::vector<FreeJob> &fr, uint32_t *pool, const std::vector<int> &phys, Flat &F)
+{
+    if (fr.empty()) return;
+    const size_t fo = F.fr.size();
+    for (FreeJob f : fr) {
+        f.in = f.in ? resolve((uint64_t)(uintptr_t)f.in, pool, phys) : nullptr;
+        f.out = resolve((uint64_t)(uintptr_t)f.out, pool, phys);
+        F.fr.push_back(f);
+    }
+    F.launches.push_back({2, fo, (int)fr.size()});
+}
+
+int ensure_path_key(velopir_ctx *c)
+{
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    if (c->path == VP_PATH_NTT && !c->bk_ntt_ready) {
+        int rc = ensure(c, c->bk_ntt, bk_ntt_words() * 4);
+        if (rc) return rc;
+        c->launches += prepare_bk_ntt(as<uint32_t>(c->bk), as<uint32_t>(c->bk_ntt), c->stream);
+        CU(cudaGetLastError());
+        c->bk_ntt_ready = true;
+    }
+    return VELOPIR_OK;
+}
+
+int launch_br(velopir_ctx *c, const BrJob *jobs, int n)
+{
+    if (c->path == VP_PATH_NTT)
+        return launch_br_ntt(jobs, n, as<uint32_t>(c->bk_ntt), as<uint32_t>(c->big), as<int>(c->errw), c->stream);
+    return launch_br_dense(jobs, n, as<uint32_t>(c->bk), as<uint32_t>(c->big), as<int>(c->errw), c->stream);
+}
+
+// Upload the flattened jobs to (br, ks, fr) device buffers and issue every launch in order.
+int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+{
+    int rc;
+    if ((rc = ensure(c, dbr, std::max<size_t>(1, F.br.size()) * sizeof(BrJob)))) return rc;
+    if ((rc = ensure(c, dks, std::max<size_t>(1, F.ks.size()) * sizeof(KsJob)))) return rc;
+    if ((rc = ensure(c, dfr, std::max<size_t>(1, F.fr.size()) * sizeof(FreeJob)))) return rc;
+    if (!F.br.empty()) CU(cudaMemcpyAsync(dbr.p, F.br.data(), F.br.size() * sizeof(BrJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.ks.empty()) CU(cudaMemcpyAsync(dks.p, F.ks.data(), F.ks.size() * sizeof(KsJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.fr.empty()) CU(cudaMemcpyAsync(dfr.p, F.fr.data(), F.fr.size() * sizeof(FreeJob), cudaMemcpyHostToDevice, c->stream));
+    for (const Launch &l : F.launches) {
+        if (l.kind == 0) c->launches += launch_br(c, as<BrJob>(dbr) + l.off, l.n);
+        else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), c->stream);
+        else c->launches += launch_free(as<FreeJob>(dfr) + l.off, l.n, c->stream);
+        CU(cudaGetLastError());
+    }
+    return VELOPIR_OK;
+}
+
+int check_device_error(velopir_ctx *c)
+{
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, c->errw.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h != kDevOk) {
+        cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->stream);
+        return fail(c, VELOPIR_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", h);
+    }
+    return VELOPIR_OK;
+}
+
+// Run a whole program synchronously with the context's shared scratch.
+int run_program(velopir_ctx *c, Program &P)
+{
+    int rc;
+    if ((rc = ensure_path_key(c))) return rc;
+    allocate_slots(P);
+    if ((rc = ensure(c, c->pool, std::max<size_t>(1, (size_t)P.nphys) * kSlotWords * 4))) return rc;
+    size_t max_br = 1;
+    for (const Layer &L : P.layers) max_br = std::max(max_br, L.br.size());
+    const int cap = (int)std::max<size_t>(2, std::min<size_t>(max_br, (size_t)c->big_rows));
+    if ((rc = ensure(c, c->big, (size_t)cap * kBigWords * 4))) return rc;
+    uint32_t *pool = as<uint32_t>(c->pool);
+    Flat F;
+    flatten_free(P.pre, pool, P.phys, F);
+    for (const Layer &L : P.layers) {
+        flatten_layer(L, cap, pool, P.phys, F);
+        flatten_free(L.fr, pool, P.phys, F);
+    }
+    if ((rc = issue(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr))) return rc;
+    return check_device_error(c);
+}
+
+// Stage `words` uint32 of a caller buffer on the device (device pointers pass through).
+int stage_in(velopir_ctx *c, const uint32_t *src, size_t words, size_t at_words, const uint32_t **dev)
+{
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return VELOPIR_OK;
+    }
+    uint32_t *d = as<uint32_t>(c->in) + at_words;
+    CU(cudaMemcpyAsync(d, src, words * 4, cudaMemcpyHostToDevice, c->stream));
+    *dev = d;
+    return VELOPIR_OK;
+}
+
+struct OutStage {
+    uint32_t *user = nullptr;
+    uint32_t *dev = nullptr;
+    size_t words = 0;
+    bool host = false;
+};
+
+int stage_out(velopir_ctx *c, uint32_t *user, size_t words, OutStage &o)
+{
+    o.user = user;
+    o.words = words;
+    o.host = !is_device_ptr(user);
+    if (o.host) {
+        int rc = ensure(c, c->out, std::max<size_t>(1, words) * 4);
+        if (rc) return rc;
+        o.dev = as<uint32_t>(c->out);
+    } else {
+        o.dev = user;
+    }
+    return VELOPIR_OK;
+}
+
+int finish_out(velopir_ctx *c, const OutStage &o)
+{
+    if (o.host && o.words) {
+        CU(cudaMemcpyAsync(o.user, o.dev, o.words * 4, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return VELOPIR_OK;
+}
+
+bool params_ok(const velopir_params *p)
+{
+    return p && p->n == kn && p->N == kN && p->k == 1 && p->l == kL && p->bg_bits == kBgBits && p->ks_t == kKsT &&
+           p->ks_base_bits == kKsBaseBits;
+}
+
+int build_batch(velopir_ctx *c, int gate, const uint32_t *din, uint32_t *dout, size_t count, Program &P)
+{
+    Builder B(P);
+    const int ar = gate == G_MUX ? 3 : 2;
+    for (size_t g = 0; g < count; ++g) {
+        const uint32_t *base = din + g * ar * kLweWords;
+        if (gate == G_MUX)
+            B.mux(B.input(base), B.input(base + kLweWords), B.input(base + 2 * kLweWords), dout + g * kLweWords);
+        else
+            B.gate(gate, B.input(base), B.input(base + kLweWords), dout + g * kLweWords);
+    }
+    return VELOPIR_OK;
+}
+
+// ------------------------------ serving -----------------------------------
+
+struct ServeQuery {
+    uint64_t ticket = 0;
+    velopir_query q{};
+    Program P;
+    size_t cursor = 0;      // next layer
+    bool pre_done = false;
+    size_t footprint = 0;
+    uint32_t *dmem = nullptr;   // inputs + pool + output staging (one allocation)
+    uint32_t *dout = nullptr;
+    size_t out_words = 0;
+    bool out_host = false;
+    bool done = false;
+    cudaEvent_t ev = nullptr;
+};
+
+size_t query_in_words(const velopir_query &q)
+{
+    switch (q.kind) {
+    case VP_QUERY_INTV: return 64 * (size_t)kLweWords;
+    case VP_QUERY_COV: return 32 * (size_t)kLweWords;
+    default: return (size_t)q.id_bits * kLweWords;
+    }
+}
+
+size_t query_out_words(const velopir_query &q)
+{
+    if (q.kind == VP_QUERY_IDM && q.payload) return (size_t)q.payload_bits * kLweWords;
+    return q.D * kLweWords;
+}
+
+int validate_query(velopir_ctx *c, const velopir_query &q)
+{
+    if (!q.enc_a || !q.out || (!q.db && q.D)) return fail(c, VELOPIR_ERR_ARG, "null query buffer");
+    if (q.kind == VP_QUERY_INTV && !q.enc_b) return fail(c, VELOPIR_ERR_ARG, "IntV needs enc_b");
+    if (q.kind < 0 || q.kind > 2) return fail(c, VELOPIR_ERR_ARG, "unknown query kind %d", q.kind);
+    if (q.kind == VP_QUERY_IDM && (q.id_bits < 1 || q.id_bits > 32))
+        return fail(c, VELOPIR_ERR_ARG, "id_bits must be in [1, 32]");
+    if (q.kind == VP_QUERY_IDM && q.payload && (q.payload_bits < 1 || q.payload_bits > 32))
+        return fail(c, VELOPIR_ERR_ARG, "payload_bits must be in [1, 32]");
+    return VELOPIR_OK;
+}
+
+// Build the query's program against its own device block: [inputs | pool | out].
+int build_query(velopir_ctx *c, ServeQuery &s)
+{
+    const velopir_query &q = s.q;
+    const size_t inw = query_in_words(q);
+    s.out_words = query_out_words(q);
+    s.out_host = !is_device_ptr(q.out);
+    // Build once with placeholder bases to learn the pool size, then rebuild.
+    for (int pass = 0; pass < 2; ++pass) {
+        s.P = Program();
+        Builder B(s.P);
+        // Pass 0 only sizes the pool: any non-null, untagged bases give the
+        // same program shape as the real ones used in pass 1.
+        uint32_t *in_base = pass == 0 ? reinterpret_cast<uint32_t *>(uintptr_t(1) << 20) : s.dmem;
+        uint32_t *out_base = s.out_host ? (pass == 0 ? reinterpret_cast<uint32_t *>(uintptr_t(1) << 40) : s.dout)
+                                        : q.out;
+        std::vector<Ref> a(64), b(32);
+        const int nin = (int)(inw / kLweWords);
+        for (int i = 0; i < nin; ++i) a[i] = B.input(in_base + (size_t)i * kLweWords);
+        if (q.kind == VP_QUERY_INTV)
+            build_intv(B, a.data(), a.data() + 32, q.db, q.D, out_base);
+        else if (q.kind == VP_QUERY_COV)
+            build_cov(B, a.data(), q.db, q.D, out_base);
+        else
+            build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out_base);
+        allocate_slots(s.P);
+        if (pass == 0) {
+            s.footprint = (inw + (s.out_host ? s.out_words : 0) + (size_t)s.P.nphys * kSlotWords) * 4 + 256;
+            if (c->budget && c->allocated + c->serve_reserved + s.footprint > c->budget) return VELOPIR_ERR_BUSY;
+            void *p = nullptr;
+            cudaError_t e = cudaMallocAsync(&p, s.footprint, c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return VELOPIR_ERR_BUSY;
+            }
+            s.dmem = reinterpret_cast<uint32_t *>(p);
+            s.dout = s.dmem + inw;
+            c->serve_reserved += s.footprint;
+            // inputs
+            CU(cudaMemcpyAsync(s.dmem, q.enc_a, (q.kind == VP_QUERY_INTV ? 32 : inw / kLweWords) * kLweWords * 4,
+                               cudaMemcpyDefault, c->stream));
+            if (q.kind == VP_QUERY_INTV)
+                CU(cudaMemcpyAsync(s.dmem + 32 * kLweWords, q.enc_b, 32 * kLweWords * 4, cudaMemcpyDefault, c->stream));
+        }
+    }
+    return VELOPIR_OK;
+}
+
+uint32_t *query_pool(const ServeQuery &s)
+{
+    return s.dmem + query_in_words(s.q) + (s.out_host ? s.out_words : 0);
+}
+
+// One serving step: every active query contributes its next layer; all of
+// them run as one merged launch sequence.
+int serve_step(velopir_ctx *c)
+{
+    int rc;
+    // admit waiting queries while memory allows
+    while (!c->waiting.empty()) {
+        ServeQuery &s = *c->waiting.front();
+        rc = build_query(c, s);
+        if (rc == VELOPIR_ERR_BUSY) break;
+        if (rc) return rc;
+        c->active.push_back(std::move(c->waiting.front()));
+        c->waiting.pop_front();
+    }
+    if (c->active.empty()) return VELOPIR_OK;
+    if ((rc = ensure_path_key(c))) return rc;
+    Flat F;
+    // Each query's layer is chunked on its own; chunks of all queries are
+    // concatenated per kind so one blind-rotation launch covers them all.
+    Flat merged;
+    size_t total_br = 0;
+    for (auto &sp : c->active) {
+        ServeQuery &s = *sp;
+        if (s.cursor < s.P.layers.size()) total_br += s.P.layers[s.cursor].br.size();
+    }
+    const int cap = (int)std::max<size_t>(2, std::min<size_t>(total_br, (size_t)c->big_rows));
+    if ((rc = ensure(c, c->big, (size_t)cap * kBigWords * 4))) return rc;
+    // Merge layer jobs of all queries into one virtual layer with rebased indices.
+    Layer ML;
+    std::vector<FreeJob> pre, post;
+    for (auto &sp : c->active) {
+        ServeQuery &s = *sp;
+        uint32_t *pool = query_pool(s);
+        if (!s.pre_done) {
+            for (FreeJob f : s.P.pre) {
+                f.in = f.in ? resolve((uint64_t)(uintptr_t)f.in, pool, s.P.phys) : nullptr;
+                f.out = resolve((uint64_t)(uintptr_t)f.out, pool, s.P.phys);
+                pre.push_back(f);
+            }
+            s.pre_done = true;
+        }
+        if (s.cursor >= s.P.layers.size()) continue;
+        const Layer &L = s.P.layers[s.cursor];
+        const int base = (int)ML.br.size();
+        for (BrJob j : L.br) {
+            j.in0 = j.in0 ? resolve((uint64_t)(uintptr_t)j.in0, pool, s.P.phys) : nullptr;
+            j.in1 = j.in1 ? resolve((uint64_t)(uintptr_t)j.in1, pool, s.P.phys) : nullptr;
+            ML.br.push_back(j);
+        }
+        for (KsJob k : L.ks) {
+            k.e0 += base;
+            if (k.e1 >= 0) k.e1 += base;
+            k.out = resolve((uint64_t)(uintptr_t)k.out, pool, s.P.phys);
+            ML.ks.push_back(k);
+        }
+        for (FreeJob f : L.fr) {
+            f.in = f.in ? resolve((uint64_t)(uintptr_t)f.in, pool, s.P.phys) : nullptr;
+            f.out = resolve((uint64_t)(uintptr_t)f.out, pool, s.P.phys);
+            post.push_back(f);
+        }
+        s.cursor++;
+    }
+    static const std::vector<int> nophys;
+    flatten_free(pre, nullptr, nophys, merged);
+    flatten_layer(ML, cap, nullptr, nophys, merged);
+    flatten_free(post, nullptr, nophys, merged);
+    if ((rc = issue(c, merged, c->s_br, c->s_ks, c->s_fr))) return rc;
+    // completion bookkeeping
+    for (auto &sp : c->active) {
+        ServeQuery &s = *sp;
+        if (s.cursor >= s.P.layers.size() && !s.ev) {
+            if (s.out_host) CU(cudaMemcpyAsync(s.q.out, s.dout, s.out_words * 4, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+            CU(cudaEventRecord(s.ev, c->stream));
+        }
+    }
+    return VELOPIR_OK;
+}
+
+int reap(velopir_ctx *c)
+{
+    for (size_t i = 0; i < c->active.size();) {
+        ServeQuery &s = *c->active[i];
+        if (s.ev && cudaEventQuery(s.ev) == cudaSuccess) {
+            int rc = check_device_error(c);
+            cudaEventDestroy(s.ev);
+            s.ev = nullptr;
+            cudaFreeAsync(s.dmem, c->stream);
+            c->serve_reserved -= s.footprint;
+            s.done = true;
+            c->finished.push_back(std::move(c->active[i]));
+            c->active.erase(c->active.begin() + i);
+            if (rc) return rc;
+        } else {
+            ++i;
+        }
+    }
+    return VELOPIR_OK;
+}
+
+}  // namespace
+
+// ================================ C ABI ====================================
+
+extern "C" {
+
+int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream)
+{
+    velopir_ctx *c = nullptr;
+    if (!out) return fail(c, VELOPIR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(c, VELOPIR_ERR_NOCUDA, "no CUDA device visible");
+    }
+    if (device < 0 || device >= n) return fail(c, VELOPIR_ERR_ARG, "device %d out of range [0, %d)", device, n);
+    if (cudaSetDevice(device) != cudaSuccess) return fail(c, VELOPIR_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    std::unique_ptr<velopir_ctx> ctx(new velopir_ctx());
+    c = ctx.get();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    int rc = ensure(c, c->errw, 256);
+    if (rc) { g_create_error = c->err; return rc; }
+    CU(cudaMemsetAsync(c->errw.p, 0, 256, c->stream));
+    *out = ctx.release();
+    return VELOPIR_OK;
+}
+
+int velopir_destroy(velopir_ctx *c)
+{
+    if (!c) return VELOPIR_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &s : c->active) {
+        if (s->ev) cudaEventDestroy(s->ev);
+        if (s->dmem) cudaFreeAsync(s->dmem, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->bk, &c->ksk, &c->bk_ntt, &c->big, &c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->pool,
+                      &c->in, &c->out, &c->errw, &c->s_br, &c->s_ks, &c->s_fr};
+    for (DevBuf *b : bufs) dev_free(c, *b);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return VELOPIR_OK;
+}
+
+int velopir_load_cloud_key(velopir_ctx *c, const velopir_params *params, const uint32_t *bk, size_t bk_words,
+                           const uint32_t *ksk, size_t ksk_words)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (!params_ok(params)) return fail(c, VELOPIR_ERR_ARG, "parameters must be n=630 N=1024 k=1 l=3 Bg=2^7 t=8 base=2^2");
+    if (!bk || !ksk) return fail(c, VELOPIR_ERR_ARG, "null key buffer");
+    if (bk_words != kBkWords) return fail(c, VELOPIR_ERR_ARG, "bk_words %zu != %zu", bk_words, kBkWords);
+    if (ksk_words != kKskAbiWords) return fail(c, VELOPIR_ERR_ARG, "ksk_words %zu != %zu", ksk_words, kKskAbiWords);
+    cudaSetDevice(c->device);
+    int rc;
+    if ((rc = ensure(c, c->bk, kBkWords * 4))) return rc;
+    if ((rc = ensure(c, c->ksk, kKskDevWords * 4))) return rc;
+    CU(cudaMemcpyAsync(c->bk.p, bk, kBkWords * 4, cudaMemcpyDefault, c->stream));
+    // The ABI rows (631 words) are padded to 632 for 16-byte loads.
+    if ((rc = ensure(c, c->in, kKskAbiWords * 4))) return rc;
+    CU(cudaMemcpyAsync(c->in.p, ksk, kKskAbiWords * 4, cudaMemcpyDefault, c->stream));
+    c->launches += launch_pad_ksk(as<uint32_t>(c->in), as<uint32_t>(c->ksk), c->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
+    c->key_loaded = true;
+    c->bk_ntt_ready = false;
+    return VELOPIR_OK;
+}
+
+int velopir_set_path(velopir_ctx *c, velopir_path path)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (path != VP_PATH_INT32_DENSE && !(path == VP_PATH_NTT && bk_ntt_words() > 0))
+        return fail(c, VELOPIR_ERR_ARG, "path %d is not available in this build", (int)path);
+    c->path = path;
+    return VELOPIR_OK;
+}
+
+static int bootstrap_common(velopir_ctx *c, velopir_gate gate, const uint32_t *lwe_in, uint32_t *lwe_out,
+                            size_t count, bool plain)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if ((int)gate < VP_AND || (int)gate > VP_MUX) return fail(c, VELOPIR_ERR_ARG, "unknown gate %d", (int)gate);
+    if (count == 0) return VELOPIR_OK;
+    if (!lwe_in || !lwe_out) return fail(c, VELOPIR_ERR_ARG, "null ciphertext buffer");
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    cudaSetDevice(c->device);
+    const int ar = gate == VP_MUX ? 3 : 2;
+    const size_t inw = count * ar * kLweWords;
+    int rc;
+    if (!is_device_ptr(lwe_in) && (rc = ensure(c, c->in, inw * 4))) return rc;
+    const uint32_t *din = nullptr;
+    if ((rc = stage_in(c, lwe_in, inw, 0, &din))) return rc;
+    OutStage o;
+    if ((rc = stage_out(c, lwe_out, count * kLweWords, o))) return rc;
+    if (!plain) {
+        Program P;
+        build_batch(c, (int)gate, din, o.dev, count, P);
+        if ((rc = run_program(c, P))) return rc;
+    } else {
+        for (size_t g = 0; g < count; ++g) {
+            Program P;
+            build_batch(c, (int)gate, din + g * ar * kLweWords, o.dev + g * kLweWords, 1, P);
+            if ((rc = run_program(c, P))) return rc;
+        }
+    }
+    return finish_out(c, o);
+}
+
+int velopir_bootstrap_batch(velopir_ctx *c, velopir_gate gate, const uint32_t *lwe_in, uint32_t *lwe_out, size_t count)
+{
+    return bootstrap_common(c, gate, lwe_in, lwe_out, count, false);
+}
+
+int velopir_bootstrap_plain(velopir_ctx *c, velopir_gate gate, const uint32_t *lwe_in, uint32_t *lwe_out, size_t count)
+{
+    return bootstrap_common(c, gate, lwe_in, lwe_out, count, true);
+}
+
+static int run_query(velopir_ctx *c, const velopir_query &q)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    int rc;
+    if ((rc = validate_query(c, q))) return rc;
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    cudaSetDevice(c->device);
+    if (q.D == 0) return VELOPIR_OK;
+    const size_t inw = query_in_words(q);
+    if ((rc = ensure(c, c->in, inw * 4))) return rc;
+    const uint32_t *din_a = nullptr, *din_b = nullptr;
+    if (q.kind == VP_QUERY_INTV) {
+        if ((rc = stage_in(c, q.enc_a, 32 * kLweWords, 0, &din_a))) return rc;
+        if ((rc = stage_in(c, q.enc_b, 32 * kLweWords, 32 * kLweWords, &din_b))) return rc;
+    } else {
+        if ((rc = stage_in(c, q.enc_a, inw, 0, &din_a))) return rc;
+    }
+    OutStage o;
+    if ((rc = stage_out(c, q.out, query_out_words(q), o))) return rc;
+    Program P;
+    Builder B(P);
+    std::vector<Ref> a(32), b(32);
+    const int na = q.kind == VP_QUERY_IDM ? q.id_bits : 32;
+    for (int i = 0; i < na; ++i) a[i] = B.input(din_a + (size_t)i * kLweWords);
+    if (q.kind == VP_QUERY_INTV)
+        for (int i = 0; i < 32; ++i) b[i] = B.input(din_b + (size_t)i * kLweWords);
+    if (q.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), q.db, q.D, o.dev);
+    else if (q.kind == VP_QUERY_COV) build_cov(B, a.data(), q.db, q.D, o.dev);
+    else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, o.dev);
+    if ((rc = run_program(c, P))) return rc;
+    return finish_out(c, o);
+}
+
+int velopir_interval_query(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, const uint32_t *rects,
+                           size_t D, uint32_t *out_bits)
+{
+    velopir_query q{};
+    q.kind = VP_QUERY_INTV;
+    q.enc_a = enc_x;
+    q.enc_b = enc_y;
+    q.db = rects;
+    q.D = D;
+    q.out = out_bits;
+    return run_query(c, q);
+}
+
+int velopir_coordinate_query(velopir_ctx *c, const uint32_t *enc_cell, const uint32_t *cells, size_t D,
+                             uint32_t *out_bits)
+{
+    velopir_query q{};
+    q.kind = VP_QUERY_COV;
+    q.enc_a = enc_cell;
+    q.db = cells;
+    q.D = D;
+    q.out = out_bits;
+    return run_query(c, q);
+}
+
+int velopir_id_match(velopir_ctx *c, const uint32_t *enc_id, int id_bits, const uint32_t *ids, size_t D,
+                     const uint32_t *payload, int payload_bits, uint32_t *out)
+{
+    velopir_query q{};
+    q.kind = VP_QUERY_IDM;
+    q.id_bits = id_bits;
+    q.payload_bits = payload ? payload_bits : 0;
+    q.enc_a = enc_id;
+    q.db = ids;
+    q.payload = payload;
+    q.D = D;
+    q.out = out;
+    return run_query(c, q);
+}
+
+int velopir_submit(velopir_ctx *c, const velopir_query *q, uint64_t *ticket)
+{
+    if (!c || !q || !ticket) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    int rc;
+    if ((rc = validate_query(c, *q))) return rc;
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    if (q->D == 0) return fail(c, VELOPIR_ERR_ARG, "empty database");
+    if (c->waiting.size() >= 4096) return fail(c, VELOPIR_ERR_BUSY, "serving queue full");
+    std::unique_ptr<ServeQuery> s(new ServeQuery());
+    s->ticket = c->next_ticket++;
+    s->q = *q;
+    *ticket = s->ticket;
+    c->waiting.push_back(std::move(s));
+    return VELOPIR_OK;
+}
+
+int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
+{
+    if (!c || !done) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    cudaSetDevice(c->device);
+    *done = 0;
+    for (auto it = c->finished.begin(); it != c->finished.end(); ++it)
+        if ((*it)->ticket == ticket) {
+            *done = 1;
+            c->finished.erase(it);
+            return VELOPIR_OK;
+        }
+    bool known = false;
+    for (auto &s : c->active) known |= s->ticket == ticket;
+    for (auto &s : c->waiting) known |= s->ticket == ticket;
+    if (!known) return fail(c, VELOPIR_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    int rc = serve_step(c);
+    if (rc) return rc;
+    // keep at most one step in flight ahead of the host
+    for (auto &s : c->active)
+        if (s->ev) cudaEventSynchronize(s->ev);
+    if ((rc = reap(c))) return rc;
+    for (auto it = c->finished.begin(); it != c->finished.end(); ++it)
+        if ((*it)->ticket == ticket) {
+            *done = 1;
+            c->finished.erase(it);
+            break;
+        }
+    return VELOPIR_OK;
+}
+
+int velopir_queue_depth(velopir_ctx *c, size_t *admitted, size_t *waiting)
+{
+    if (!c || !admitted || !waiting) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    *admitted = c->active.size();
+    *waiting = c->waiting.size();
+    return VELOPIR_OK;
+}
+
+int velopir_sync(velopir_ctx *c)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    cudaSetDevice(c->device);
+    CU(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+const char *velopir_last_error(velopir_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+uint64_t velopir_launch_count(velopir_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

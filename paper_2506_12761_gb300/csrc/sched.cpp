@@ -1,0 +1,245 @@
+// Gate-layer scheduler for the circuits of VeLoPIR's three modes (see sched.h).
+#include "sched.h"
+
+#include <algorithm>
+
+namespace vp {
+
+void gate_combination(int gate, uint32_t *cst, int32_t *s1, int32_t *s2)
+{
+    const uint32_t e = kMu, q = 2 * kMu;  // 1/8, 1/4
+    switch (gate) {
+    case G_AND:   *cst = 0u - e; *s1 = 1;  *s2 = 1;  break;  // Section 2.2: (0,-1/8)+ct1+ct2
+    case G_NAND:  *cst = e;      *s1 = -1; *s2 = -1; break;
+    case G_OR:    *cst = e;      *s1 = 1;  *s2 = 1;  break;
+    case G_NOR:   *cst = 0u - e; *s1 = -1; *s2 = -1; break;
+    case G_XOR:   *cst = q;      *s1 = 2;  *s2 = 2;  break;
+    case G_XNOR:  *cst = 0u - q; *s1 = -2; *s2 = -2; break;
+    case G_ANDNY: *cst = 0u - e; *s1 = -1; *s2 = 1;  break;
+    case G_ANDYN: *cst = 0u - e; *s1 = 1;  *s2 = -1; break;
+    case G_ORNY:  *cst = e;      *s1 = -1; *s2 = 1;  break;
+    case G_ORYN:  *cst = e;      *s1 = 1;  *s2 = -1; break;
+    default:      *cst = 0;      *s1 = 0;  *s2 = 0;  break;
+    }
+}
+
+Layer &Builder::layer(int i)
+{
+    while ((int)P.layers.size() <= i) P.layers.emplace_back();
+    return P.layers[i];
+}
+
+int Builder::new_slot(int def)
+{
+    P.slot_def.push_back(def);
+    P.slot_last.push_back(def);
+    return (int)P.slot_def.size() - 1;
+}
+
+void Builder::use(const Ref &r, int l)
+{
+    if (r.src & kSlotTag) {
+        const int v = (int)(r.src & ~kSlotTag);
+        P.slot_last[v] = std::max(P.slot_last[v], l);
+    }
+}
+
+static void add_term(BrJob &j, int which, const Ref &r, int32_t g)
+{
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(r.src);
+    const int32_t s = r.src ? g * r.sign : 0;
+    if (which == 0) { j.in0 = r.src ? p : nullptr; j.s0 = s; }
+    else { j.in1 = r.src ? p : nullptr; j.s1 = s; }
+    j.cst += (uint32_t)g * r.cst;
+}
+
+Ref Builder::gate(int g, const Ref &a, const Ref &b, uint32_t *out)
+{
+    const int l = std::max(a.ready, b.ready);
+    uint32_t gc;
+    int32_t g1, g2;
+    gate_combination(g, &gc, &g1, &g2);
+    BrJob j{};
+    j.cst = gc;
+    add_term(j, 0, a, g1);
+    add_term(j, 1, b, g2);
+    use(a, l);
+    use(b, l);
+    Layer &L = layer(l);
+    KsJob k{};
+    k.e0 = (int32_t)L.br.size();
+    k.e1 = -1;
+    L.br.push_back(j);
+    const uint64_t dst = out ? (uint64_t)(uintptr_t)out : (kSlotTag | (uint64_t)new_slot(l));
+    k.out = reinterpret_cast<uint32_t *>(dst);
+    L.ks.push_back(k);
+    P.bootstraps += 1;
+    P.gates += 1;
+    Ref r;
+    r.src = dst;
+    r.sign = 1;
+    r.ready = l + 1;
+    return r;
+}
+
+Ref Builder::mux(const Ref &c, const Ref &a, const Ref &b, uint32_t *out)
+{
+    const int l = std::max(c.ready, std::max(a.ready, b.ready));
+    BrJob j0{}, j1{};
+    j0.cst = 0u - kMu;                 // AND(c, a)
+    add_term(j0, 0, c, 1);
+    add_term(j0, 1, a, 1);
+    j1.cst = 0u - kMu;                 // AND(NOT c, b)
+    add_term(j1, 0, c, -1);
+    add_term(j1, 1, b, 1);
+    use(c, l);
+    use(a, l);
+    use(b, l);
+    Layer &L = layer(l);
+    KsJob k{};
+    k.e0 = (int32_t)L.br.size();
+    k.e1 = k.e0 + 1;
+    k.cst = kMu;                       // + T(1/8) before the key switch
+    L.br.push_back(j0);
+    L.br.push_back(j1);
+    const uint64_t dst = out ? (uint64_t)(uintptr_t)out : (kSlotTag | (uint64_t)new_slot(l));
+    k.out = reinterpret_cast<uint32_t *>(dst);
+    L.ks.push_back(k);
+    P.bootstraps += 2;
+    P.gates += 1;
+    Ref r;
+    r.src = dst;
+    r.sign = 1;
+    r.ready = l + 1;
+    return r;
+}
+
+void Builder::materialize(const Ref &r, uint32_t *out)
+{
+    FreeJob f{};
+    f.in = r.src ? reinterpret_cast<const uint32_t *>(r.src) : nullptr;
+    f.s = r.src ? r.sign : 0;
+    f.cst = r.cst;
+    f.out = out;
+    if (r.ready == 0) {
+        P.pre.push_back(f);
+    } else {
+        use(r, r.ready - 1);
+        layer(r.ready - 1).fr.push_back(f);
+    }
+}
+
+// XNOR against a plaintext bit is free: v ? x : NOT x.
+static Ref xnor_plain(const Ref &x, int bit) { return bit ? x : Builder::neg(x); }
+
+Ref build_compare(Builder &B, const Ref *x, int l, uint64_t plain, bool plain_first, bool strict, bool is_unsigned)
+{
+    // Alg. HomCompLeOPT / HomCompL with the plaintext operand's XNORs and MUXes
+    // reduced to one gate each (c ? a : b by cases on the plaintext bit).
+    Ref top = x[l - 1];
+    if (is_unsigned) {
+        plain ^= 1ull << (l - 1);
+        top = Builder::neg(top);
+    }
+    Ref t = Builder::trivial(strict ? 0u - kMu : kMu);
+    for (int i = 0; i <= l - 2; ++i) {
+        const int bit = (int)((plain >> i) & 1);
+        const int g = plain_first ? (bit ? G_AND : G_OR) : (bit ? G_ORNY : G_ANDNY);
+        t = B.gate(g, x[i], t);
+    }
+    const int tb = (int)((plain >> (l - 1)) & 1);
+    const int g = plain_first ? (tb ? G_ORNY : G_ANDNY) : (tb ? G_AND : G_OR);
+    return B.gate(g, top, t);
+}
+
+Ref build_eq_plain(Builder &B, const Ref *x, int l, uint64_t v, uint32_t *out)
+{
+    // Alg. HomEqOPT: free XNORs, then t[i] = AND(t[i], t[i+k]) for k = 1, 2, 4, ...
+    std::vector<Ref> t(l);
+    for (int i = 0; i < l; ++i) t[i] = xnor_plain(x[i], (int)((v >> i) & 1));
+    int last_k = 0;
+    for (int k = 1; k < l; k *= 2) last_k = k;
+    for (int k = 1; k < l; k *= 2)
+        for (int i = 0; i + k < l; i += 2 * k)
+            t[i] = B.gate(G_AND, t[i], t[i + k], (out && k == last_k && i == 0) ? out : nullptr);
+    if (out && l == 1) B.materialize(t[0], out);
+    return t[0];
+}
+
+void build_intv(Builder &B, const Ref *x, const Ref *y, const uint32_t *rects, size_t D, uint32_t *out)
+{
+    // Alg. InterValid: v = AND(AND(LE(x_lo,x), L(x,x_hi)), AND(LE(y_lo,y), L(y,y_hi))).
+    for (size_t d = 0; d < D; ++d) {
+        const uint32_t *r = rects + 4 * d;
+        Ref vxl = build_compare(B, x, 32, r[0], true, false, true);
+        Ref vxr = build_compare(B, x, 32, r[1], false, true, true);
+        Ref vyl = build_compare(B, y, 32, r[2], true, false, true);
+        Ref vyr = build_compare(B, y, 32, r[3], false, true, true);
+        Ref vx = B.gate(G_AND, vxl, vxr);
+        Ref vy = B.gate(G_AND, vyl, vyr);
+        B.gate(G_AND, vx, vy, out + d * kLweWords);
+    }
+}
+
+void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uint32_t *out)
+{
+    // Alg. CoV: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)), 16 + 16 bits.
+    for (size_t d = 0; d < D; ++d) {
+        Ref vx = build_eq_plain(B, cell, 16, cells[d] & 0xFFFFu);
+        Ref vy = build_eq_plain(B, cell + 16, 16, cells[d] >> 16);
+        B.gate(G_AND, vx, vy, out + d * kLweWords);
+    }
+}
+
+void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
+               int payload_bits, uint32_t *out)
+{
+    if (!payload) {
+        for (size_t d = 0; d < D; ++d) build_eq_plain(B, id, id_bits, ids[d], out + d * kLweWords);
+        return;
+    }
+    // Match bits, free zero-out with each plaintext payload bit (Alg.
+    // HomBitwiseAND: AND(v, 1) = v, AND(v, 0) = Enc(0) trivially), then the
+    // pairwise HomSum XOR reduction of Section 5 per payload bit.
+    std::vector<Ref> v(D);
+    for (size_t d = 0; d < D; ++d) v[d] = build_eq_plain(B, id, id_bits, ids[d]);
+    std::vector<Ref> S(D * (size_t)payload_bits);
+    for (size_t d = 0; d < D; ++d)
+        for (int j = 0; j < payload_bits; ++j)
+            S[d * payload_bits + j] = ((payload[d] >> j) & 1u) ? v[d] : Builder::trivial(0u - kMu);
+    size_t last_k = 0;
+    for (size_t k = 1; k < D; k *= 2) last_k = k;
+    for (size_t k = 1; k < D; k *= 2)
+        for (size_t i = 0; i + k < D; i += 2 * k)
+            for (int j = 0; j < payload_bits; ++j) {
+                uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
+            }
+    if (D == 1)
+        for (int j = 0; j < payload_bits; ++j) B.materialize(S[j], out + (size_t)j * kLweWords);
+}
+
+void allocate_slots(Program &p)
+{
+    const int nv = (int)p.slot_def.size();
+    const int nl = (int)p.layers.size();
+    std::vector<std::vector<int>> defs(nl + 1), lasts(nl + 1);
+    for (int v = 0; v < nv; ++v) {
+        defs[p.slot_def[v]].push_back(v);
+        lasts[p.slot_last[v]].push_back(v);
+    }
+    p.phys.assign(nv, -1);
+    std::vector<int> freelist;
+    int next = 0;
+    for (int l = 0; l < nl; ++l) {
+        if (l > 0)
+            for (int v : lasts[l - 1]) freelist.push_back(p.phys[v]);
+        for (int v : defs[l]) {
+            if (!freelist.empty()) { p.phys[v] = freelist.back(); freelist.pop_back(); }
+            else p.phys[v] = next++;
+        }
+    }
+    p.nphys = next;
+}
+
+}  // namespace vp

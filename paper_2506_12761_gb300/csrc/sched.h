@@ -1,0 +1,84 @@
+// Gate-layer scheduler: circuits of the three VeLoPIR modes as layered gate
+// programs whose every layer is issued as one batch of bootstraps.
+//
+// A circuit is built over Refs: c = sign * [src] + T(cst), where src is a
+// stored ciphertext (device address, or a virtual pool slot) or nothing (a
+// trivial ciphertext).  Bootstrap-free gates (NOT, XNOR/AND against a
+// plaintext bit, trivial constants) only transform Refs; they are folded into
+// the pre-combination of the next bootstrap, which is the same mod-2^32
+// arithmetic as materialising them first.  Each bootstrapped gate is placed
+// in layer max(ready(inputs)) (as-soon-as-possible), so the layers of many
+// database entries and of many queries merge into shared launches.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "vp_internal.h"
+
+namespace vp {
+
+constexpr uint64_t kSlotTag = 1ull << 63;
+
+struct Ref {
+    uint64_t src = 0;   // device address, or kSlotTag | virtual slot, or 0 (trivial)
+    int32_t sign = 0;
+    uint32_t cst = 0;
+    int32_t ready = 0;  // the layer index from which src may be read
+};
+
+struct Layer {
+    std::vector<BrJob> br;   // pointers may carry kSlotTag
+    std::vector<KsJob> ks;   // e0/e1 index `br` of this layer
+    std::vector<FreeJob> fr; // run after this layer's key switches
+};
+
+struct Program {
+    std::vector<Layer> layers;
+    std::vector<FreeJob> pre;   // free gates on inputs, before layer 0
+    std::vector<int> slot_def;  // layer whose key switch writes the virtual slot
+    std::vector<int> slot_last; // last layer that reads it
+    size_t bootstraps = 0;      // blind rotations
+    size_t gates = 0;           // key switches
+    int nphys = 0;              // physical slots after allocation
+    std::vector<int> phys;      // virtual -> physical slot
+};
+
+enum GateKind { G_AND = 0, G_NAND, G_OR, G_NOR, G_XOR, G_XNOR, G_ANDNY, G_ANDYN, G_ORNY, G_ORYN, G_MUX };
+
+// Linear pre-combination of a binary gate: T(cst) + s1*c1 + s2*c2.
+void gate_combination(int gate, uint32_t *cst, int32_t *s1, int32_t *s2);
+
+class Builder {
+public:
+    explicit Builder(Program &p) : P(p) {}
+    Ref input(const uint32_t *dev) const { Ref r; r.src = (uint64_t)(uintptr_t)dev; r.sign = 1; return r; }
+    static Ref trivial(uint32_t mu) { Ref r; r.cst = mu; return r; }
+    static Ref neg(const Ref &a) { Ref r = a; r.sign = -a.sign; r.cst = 0u - a.cst; return r; }
+    // Bootstrapped binary gate; out == nullptr stores the result in a new pool slot.
+    Ref gate(int g, const Ref &a, const Ref &b, uint32_t *out = nullptr);
+    // MUX(c, a, b) = c ? a : b with two blind rotations and one key switch.
+    Ref mux(const Ref &c, const Ref &a, const Ref &b, uint32_t *out = nullptr);
+    // Write the value of a Ref into `out` (device) without a bootstrap.
+    void materialize(const Ref &r, uint32_t *out);
+
+private:
+    Layer &layer(int i);
+    int new_slot(int def);
+    void use(const Ref &r, int layer);
+    Program &P;
+};
+
+// Circuits with a plaintext database (bits LSB first).
+// a <= x (plain_first) or x < b, unsigned through the top-bit flip.
+Ref build_compare(Builder &B, const Ref *x, int l, uint64_t plain, bool plain_first, bool strict, bool is_unsigned);
+Ref build_eq_plain(Builder &B, const Ref *x, int l, uint64_t v, uint32_t *out = nullptr);
+void build_intv(Builder &B, const Ref *x, const Ref *y, const uint32_t *rects, size_t D, uint32_t *out);
+void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uint32_t *out);
+void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
+               int payload_bits, uint32_t *out);
+
+// Liveness-based assignment of virtual slots to physical pool slots: a slot is
+// reused only in a layer after the last layer that reads its previous value.
+void allocate_slots(Program &p);
+
+}  // namespace vp

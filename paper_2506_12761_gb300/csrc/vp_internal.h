@@ -1,0 +1,84 @@
+// Internal declarations of libvelopir.so (not part of the public ABI).
+//
+// Parameters are fixed at compile time to the TFHE 128-bit set the paper uses
+// (Appendix parameter table): n = 630, N = 1024, k = 1, l = 3, Bg = 2^7,
+// key-switch base 2^2 with t = 8 levels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vp {
+
+constexpr int kN = 1024;            // ring degree
+constexpr int kTwoN = 2 * kN;
+constexpr int kn = 630;             // LWE dimension
+constexpr int kLweWords = kn + 1;   // ABI ciphertext length
+constexpr int kSlotWords = 632;     // device-internal ciphertext stride (16-byte rows)
+constexpr int kL = 3;               // gadget levels
+constexpr int kBgBits = 7;
+constexpr int kRows = 2 * kL;       // TRGSW rows
+constexpr int kKsT = 8;             // key-switch levels
+constexpr int kKsBaseBits = 2;
+constexpr int kKsBase = 1 << kKsBaseBits;
+constexpr int kBigWords = 1028;     // extracted LWE (N + 1 words) row stride
+constexpr uint32_t kMu = 1u << 29;  // 1/8
+constexpr size_t kBkStepWords = (size_t)kRows * 2 * kN;          // 12288 words = 48 KB
+constexpr size_t kBkWords = (size_t)kn * kBkStepWords;
+constexpr size_t kKskAbiWords = (size_t)kN * kKsT * kKsBase * kLweWords;
+constexpr int kKskQuads = kSlotWords / 4;                         // 158 uint4 per padded row
+constexpr size_t kKskDevWords = (size_t)kN * kKsT * kKsBase * kSlotWords;
+
+// Gate pre-combination of one blind rotation: c = s0*in0 + s1*in1 + T(cst).
+// A null input contributes nothing.  The extracted result goes to scratch
+// row `big`.
+struct BrJob {
+    const uint32_t *in0;
+    const uint32_t *in1;
+    int32_t s0, s1;
+    uint32_t cst;
+    int32_t big;
+};
+static_assert(sizeof(BrJob) == 32, "BrJob layout");
+
+// Key switch of e0 (+ e1) + T(cst) (extracted rows of this chunk) into `out`
+// (631 words).  e1 < 0 means a single input.
+struct KsJob {
+    int32_t e0, e1;
+    uint32_t cst;
+    int32_t pad;
+    uint32_t *out;
+    uint64_t pad2;
+};
+static_assert(sizeof(KsJob) == 32, "KsJob layout");
+
+// A gate that needs no bootstrap: out = s*in + T(cst) (NOT, copy, XNOR or
+// AND against a plaintext bit, trivial constants).
+struct FreeJob {
+    const uint32_t *in;
+    uint32_t *out;
+    int32_t s;
+    uint32_t cst;
+    uint64_t pad;
+};
+static_assert(sizeof(FreeJob) == 32, "FreeJob layout");
+
+// Device-side error codes written to the context's error word.
+enum : int { kDevOk = 0, kDevTimeout = 1 };
+
+// ---- kernel launchers (each returns the number of kernel launches issued) ----
+int launch_br_dense(const BrJob *jobs, int njobs, const uint32_t *bk, uint32_t *big, int *err,
+                    cudaStream_t st);
+int br_dense_jobs_per_cta();
+
+int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err,
+                  cudaStream_t st);
+int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st);
+size_t bk_ntt_words();
+
+int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev,
+                      cudaStream_t st);
+int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st);
+int launch_pad_ksk(const uint32_t *ksk_abi, uint32_t *ksk_dev, cudaStream_t st);
+
+}  // namespace vp

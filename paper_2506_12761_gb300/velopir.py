@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libvelopir.so (include/velopir.h), same names.
+
+Argument marshalling only: every step of gate bootstrapping and of the mode
+circuits runs in the library's CUDA kernels.  Buffers may be numpy arrays
+(host memory) or torch tensors (host or CUDA memory); torch is used only
+for device memory and streams.  There is no CPU fallback: if the compiled
+library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libvelopir.so")
+
+VELOPIR_OK = 0
+ERRORS = {-1: "ERR_ARG", -2: "ERR_NOKEY", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_BUSY",
+          -7: "ERR_NOCUDA"}
+(VP_AND, VP_NAND, VP_OR, VP_NOR, VP_XOR, VP_XNOR, VP_ANDNY, VP_ANDYN, VP_ORNY, VP_ORYN, VP_MUX) = range(11)
+VP_PATH_INT32_DENSE, VP_PATH_NTT, VP_PATH_TENSOR_F16 = 0, 1, 2
+VP_QUERY_INTV, VP_QUERY_COV, VP_QUERY_IDM = 0, 1, 2
+LWE_WORDS = 631
+BK_WORDS = 630 * 6 * 2 * 1024
+KSK_WORDS = 1024 * 8 * 4 * 631
+
+# Every symbol include/velopir.h declares.
+EXPORTS = [
+    "velopir_create", "velopir_destroy", "velopir_load_cloud_key", "velopir_set_path",
+    "velopir_bootstrap_batch", "velopir_bootstrap_plain", "velopir_interval_query",
+    "velopir_coordinate_query", "velopir_id_match", "velopir_submit", "velopir_poll",
+    "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
+    "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
+]
+
+
+class VelopirError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("n", "N", "k", "l", "bg_bits", "ks_t", "ks_base_bits")]
+
+
+def paper_params() -> Params:
+    return Params(630, 1024, 1, 3, 7, 8, 2)
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("id_bits", ctypes.c_int32), ("payload_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("enc_a", ctypes.c_void_p), ("enc_b", ctypes.c_void_p),
+                ("db", ctypes.c_void_p), ("payload", ctypes.c_void_p), ("D", ctypes.c_size_t),
+                ("out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} is missing: build it with paper_2506_12761_gb300.build.build()")
+        L = ctypes.CDLL(LIB)
+        vp, sz, i, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64
+        sig = {
+            "velopir_create": (i, [ctypes.POINTER(vp), i, sz, vp]),
+            "velopir_destroy": (i, [vp]),
+            "velopir_load_cloud_key": (i, [vp, ctypes.POINTER(Params), vp, sz, vp, sz]),
+            "velopir_set_path": (i, [vp, i]),
+            "velopir_bootstrap_batch": (i, [vp, i, vp, vp, sz]),
+            "velopir_bootstrap_plain": (i, [vp, i, vp, vp, sz]),
+            "velopir_interval_query": (i, [vp, vp, vp, vp, sz, vp]),
+            "velopir_coordinate_query": (i, [vp, vp, vp, sz, vp]),
+            "velopir_id_match": (i, [vp, vp, i, vp, sz, vp, i, vp]),
+            "velopir_submit": (i, [vp, ctypes.POINTER(Query), ctypes.POINTER(u64)]),
+            "velopir_poll": (i, [vp, u64, ctypes.POINTER(i)]),
+            "velopir_queue_depth": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+            "velopir_sync": (i, [vp]),
+            "velopir_last_error": (ctypes.c_char_p, [vp]),
+            "velopir_launch_count": (u64, [vp]),
+            "velopir_client_keygen": (i, [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+            "velopir_client_encrypt_bits": (i, [vp, vp, vp, vp, sz, vp]),
+            "velopir_client_decrypt_bits": (i, [vp, vp, sz, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def ptr(buf) -> int | None:
+    """Address of a numpy array or torch tensor (contiguous uint32 / int32 data)."""
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"] and buf.dtype.itemsize == 4, "need a contiguous 32-bit array"
+        return buf.ctypes.data
+    assert buf.is_contiguous() and buf.element_size() == 4, "need a contiguous 32-bit tensor"
+    return buf.data_ptr()
+
+
+def _check(ctx, rc: int):
+    if rc != VELOPIR_OK:
+        msg = lib().velopir_last_error(ctx)
+        raise VelopirError(rc, msg.decode() if msg else "")
+
+
+# ---- the C ABI, one function each -----------------------------------------
+
+def velopir_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
+    h = ctypes.c_void_p()
+    rc = lib().velopir_create(ctypes.byref(h), device, hbm_budget_bytes, cuda_stream)
+    _check(None, rc)
+    return h.value
+
+
+def velopir_destroy(ctx) -> None:
+    _check(ctx, lib().velopir_destroy(ctx))
+
+
+def velopir_load_cloud_key(ctx, bk, ksk, params: Params | None = None) -> None:
+    p = params or paper_params()
+    _check(ctx, lib().velopir_load_cloud_key(ctx, ctypes.byref(p), ptr(bk), BK_WORDS, ptr(ksk), KSK_WORDS))
+
+
+def velopir_set_path(ctx, path: int) -> None:
+    _check(ctx, lib().velopir_set_path(ctx, path))
+
+
+def velopir_bootstrap_batch(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
+    _check(ctx, lib().velopir_bootstrap_batch(ctx, gate, ptr(lwe_in), ptr(lwe_out), count))
+
+
+def velopir_bootstrap_plain(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
+    _check(ctx, lib().velopir_bootstrap_plain(ctx, gate, ptr(lwe_in), ptr(lwe_out), count))
+
+
+def velopir_interval_query(ctx, enc_x, enc_y, rects, D: int, out_bits) -> None:
+    _check(ctx, lib().velopir_interval_query(ctx, ptr(enc_x), ptr(enc_y), ptr(rects), D, ptr(out_bits)))
+
+
+def velopir_coordinate_query(ctx, enc_cell, cells, D: int, out_bits) -> None:
+    _check(ctx, lib().velopir_coordinate_query(ctx, ptr(enc_cell), ptr(cells), D, ptr(out_bits)))
+
+
+def velopir_id_match(ctx, enc_id, id_bits: int, ids, D: int, payload, payload_bits: int, out) -> None:
+    _check(ctx, lib().velopir_id_match(ctx, ptr(enc_id), id_bits, ptr(ids), D, ptr(payload), payload_bits, ptr(out)))
+
+
+def velopir_submit(ctx, query: Query) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, lib().velopir_submit(ctx, ctypes.byref(query), ctypes.byref(t)))
+    return t.value
+
+
+def velopir_poll(ctx, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(ctx, lib().velopir_poll(ctx, ticket, ctypes.byref(d)))
+    return bool(d.value)
+
+
+def velopir_queue_depth(ctx) -> tuple[int, int]:
+    a, w = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(ctx, lib().velopir_queue_depth(ctx, ctypes.byref(a), ctypes.byref(w)))
+    return a.value, w.value
+
+
+def velopir_sync(ctx) -> None:
+    _check(ctx, lib().velopir_sync(ctx))
+
+
+def velopir_last_error(ctx) -> str:
+    m = lib().velopir_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def velopir_launch_count(ctx) -> int:
+    return int(lib().velopir_launch_count(ctx))
+
+
+def velopir_client_keygen(km, params: Params | None = None):
+    """Cloud key (bk, ksk) as numpy arrays from synth.KeyMaterial."""
+    p = params or paper_params()
+    c = {k: np.ascontiguousarray(getattr(km, k), dtype=np.uint32) for k in ("s", "K", "bk_a", "bk_e", "ksk_a", "ksk_e")}
+    bk = np.empty(BK_WORDS, dtype=np.uint32)
+    ksk = np.empty(KSK_WORDS, dtype=np.uint32)
+    rc = lib().velopir_client_keygen(ctypes.byref(p), ptr(c["s"]), ptr(c["K"]), ptr(c["bk_a"]), ptr(c["bk_e"]),
+                                     ptr(c["ksk_a"]), ptr(c["ksk_e"]), ptr(bk), ptr(ksk))
+    _check(None, rc)
+    return bk, ksk
+
+
+def velopir_client_encrypt_bits(s, bits, lwe_mat) -> np.ndarray:
+    bits = np.ascontiguousarray(np.asarray(bits, dtype=np.uint32).reshape(-1))
+    n = len(bits)
+    a = np.ascontiguousarray(lwe_mat.a[:n], dtype=np.uint32)
+    e = np.ascontiguousarray(lwe_mat.e[:n], dtype=np.uint32)
+    out = np.empty((n, LWE_WORDS), dtype=np.uint32)
+    _check(None, lib().velopir_client_encrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(bits),
+                                                   ptr(a), ptr(e), n, ptr(out)))
+    return out
+
+
+def velopir_client_decrypt_bits(s, ct) -> np.ndarray:
+    ct = np.ascontiguousarray(np.asarray(ct, dtype=np.uint32).reshape(-1, LWE_WORDS))
+    out = np.empty(ct.shape[0], dtype=np.uint32)
+    _check(None, lib().velopir_client_decrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(ct),
+                                                   ct.shape[0], ptr(out)))
+    return out
+
+
+class Context:
+    """Owning wrapper: one velopir_ctx on one device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
+        self.h = velopir_create(device, hbm_budget_bytes, cuda_stream)
+
+    def close(self):
+        if self.h:
+            velopir_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

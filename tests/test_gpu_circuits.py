@@ -1,0 +1,77 @@
+"""GPU parity of the three mode circuits against the oracle, bit for bit,
+through the C ABI; plus decryption against the plaintext predicates."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import encrypt_value_bits, gpu_ctx
+from paper_2506_12761_gb300 import synth
+from paper_2506_12761_gb300 import velopir as vp
+
+pytestmark = pytest.mark.gpu
+
+
+def test_idm8_d4_whole_circuit(paper_keys):
+    """Identifier matching, 8-bit id, D = 4 (28 bootstraps in layers 16/8/4)."""
+    ctx, s = gpu_ctx()
+    w = synth.idm_workload(4, 8)
+    x = encrypt_value_bits(s, w["query"], 8, 500)
+    ids = w["ids"].astype(np.uint32)
+    out = np.zeros((4, 631), dtype=np.uint32)
+    vp.velopir_id_match(ctx.h, x, 8, ids, 4, None, 0, out)
+    assert np.array_equal(out, oracle.idm_batch(paper_keys, x, ids))
+    assert list(vp.velopir_client_decrypt_bits(s, out)) == [int(i == w["query"]) for i in ids]
+
+
+def test_intv_small_whole_circuit(paper_keys):
+    ctx, s = gpu_ctx()
+    w = synth.intv_workload(3, substream=1)
+    rects = w["rects"].copy()
+    rects[0] = [max(0, w["x"] - 5), w["x"] + 5, max(0, w["y"] - 9), w["y"] + 1]  # contains the point
+    cx = encrypt_value_bits(s, w["x"], 32, 501)
+    cy = encrypt_value_bits(s, w["y"], 32, 502)
+    out = np.zeros((3, 631), dtype=np.uint32)
+    vp.velopir_interval_query(ctx.h, cx, cy, rects, 3, out)
+    assert np.array_equal(out, oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
+    want = [int(r[0] <= w["x"] < r[1] and r[2] <= w["y"] < r[3]) for r in rects.astype(np.int64)]
+    assert list(vp.velopir_client_decrypt_bits(s, out)) == want and want[0] == 1
+
+
+def test_cov_small_whole_circuit(paper_keys):
+    ctx, s = gpu_ctx()
+    w = synth.cov_workload(3, substream=2)
+    cell = encrypt_value_bits(s, w["cell"], 32, 503)
+    cells = w["cells"].astype(np.uint32)
+    out = np.zeros((3, 631), dtype=np.uint32)
+    vp.velopir_coordinate_query(ctx.h, cell, cells, 3, out)
+    assert np.array_equal(out, oracle.cov_batch(paper_keys, cell, cells))
+    assert list(vp.velopir_client_decrypt_bits(s, out)) == [int(c == w["cell"]) for c in cells]
+
+
+def test_idm32_payload_aggregation(paper_keys):
+    ctx, s = gpu_ctx()
+    w = synth.idm_workload(5, 32, distinct=True, payload=True, substream=3)
+    x = encrypt_value_bits(s, w["query"], 32, 504)
+    ids = w["ids"].astype(np.uint32)
+    pay = w["payload"].astype(np.uint32)
+    out = np.zeros((32, 631), dtype=np.uint32)
+    vp.velopir_id_match(ctx.h, x, 32, ids, 5, pay, 32, out)
+    assert np.array_equal(out, oracle.idm_payload(paper_keys, x, ids, pay, 32))
+    got = vp.velopir_client_decrypt_bits(s, out)
+    assert int(sum(int(b) << j for j, b in enumerate(got))) == int(pay[w["planted"]])
+
+
+def test_degenerate_shapes(paper_keys):
+    ctx, s = gpu_ctx()
+    # id_bits = 1: no bootstrap at all (plaintext XNOR is free)
+    x = encrypt_value_bits(s, 1, 1, 505)
+    out = np.zeros((2, 631), dtype=np.uint32)
+    vp.velopir_id_match(ctx.h, x, 1, np.array([1, 0], dtype=np.uint32), 2, None, 0, out)
+    assert np.array_equal(out, oracle.idm_batch(paper_keys, x, [1, 0]))
+    # D = 1 with payload: no XOR layer
+    x = encrypt_value_bits(s, 3, 2, 506)
+    out = np.zeros((4, 631), dtype=np.uint32)
+    vp.velopir_id_match(ctx.h, x, 2, np.array([3], dtype=np.uint32), 1, np.array([9], dtype=np.uint32), 4, out)
+    assert np.array_equal(out, oracle.idm_payload(paper_keys, x, [3], [9], 4))
+    # D = 0: nothing to do
+    vp.velopir_id_match(ctx.h, x, 2, np.zeros(1, dtype=np.uint32), 0, None, 0, out)
