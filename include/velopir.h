@@ -18,8 +18,10 @@
  *    velopir_last_error() then describes the failure.  No function aborts.
  *  - Buffers belong to the caller.  A pointer may be host or device memory
  *    (classified with cudaPointerGetAttributes); results are written to the
- *    memory kind the caller passed.  Host buffers are staged through device
- *    scratch owned by the context.
+ *    memory kind the caller passed.  Host ciphertext buffers are staged
+ *    through device scratch owned by the context; plaintext databases are
+ *    read on the host (the scheduler compiles them into the gate program),
+ *    so a device-resident database is first copied to the host.
  *  - Calls on one context are serialised on the context's CUDA stream and are
  *    synchronous unless stated otherwise (velopir_submit is asynchronous).
  *  - A context is not thread-safe; use one context per host thread.
@@ -154,7 +156,7 @@ int velopir_coordinate_query(velopir_ctx *ctx, const uint32_t *enc_cell, const u
 int velopir_id_match(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, const uint32_t *ids,
                      size_t D, const uint32_t *payload, int payload_bits, uint32_t *out);
 
-/* ---- serving: asynchronous queries with continuous batching ------------- */
+/* ---- several queries as one program --------------------------------------- */
 
 typedef enum { VP_QUERY_INTV = 0, VP_QUERY_COV = 1, VP_QUERY_IDM = 2 } velopir_query_kind;
 
@@ -165,11 +167,25 @@ typedef struct {
     int32_t reserved;
     const uint32_t *enc_a;   /* IntV: enc_x; CoV: enc_cell; IdM: enc_id (host or device) */
     const uint32_t *enc_b;   /* IntV: enc_y; otherwise NULL */
-    const uint32_t *db;      /* rects / cells / ids (host memory) */
-    const uint32_t *payload; /* IdM payloads (host memory) or NULL */
+    const uint32_t *db;      /* rects / cells / ids (host or device; copied at submit) */
+    const uint32_t *payload; /* IdM payloads (host or device; copied at submit) or NULL */
     size_t D;
     uint32_t *out;           /* result buffer, same shapes as the synchronous calls */
 } velopir_query;
+
+/* Run nq queries (of any modes and database sizes) as one gate program: the
+ * layers of all queries are packed into shared launches (Section 5's
+ * outermost parallelism across entries, extended across queries).  Buffers
+ * as in velopir_submit; results are in each q->out on return.  use_graph != 0
+ * captures the launch sequence into a CUDA graph and replays it while the
+ * next batch has the same launch list (same modes, sizes and plaintext
+ * shapes).  Errors: as the synchronous query calls. */
+int velopir_query_batch(velopir_ctx *ctx, const velopir_query *queries, size_t nq, int use_graph);
+
+/* How many times a captured graph was replayed instead of re-captured. */
+uint64_t velopir_graph_replays(velopir_ctx *ctx);
+
+/* ---- serving: asynchronous queries with continuous batching ------------- */
 
 /* Enqueue a query.  It is admitted into the running batch as soon as the
  * context's HBM budget allows; its gate layers are merged with those of every
@@ -195,6 +211,21 @@ const char *velopir_last_error(velopir_ctx *ctx);
 
 /* Kernel launches this context has issued since creation (for launch counting). */
 uint64_t velopir_launch_count(velopir_ctx *ctx);
+
+/* ---- tracing: per-kernel device time -------------------------------------- */
+
+typedef enum { VP_KERNEL_BLIND_ROTATE = 0, VP_KERNEL_KEY_SWITCH = 1, VP_KERNEL_FREE = 2 } velopir_kernel;
+
+/* enable != 0: bracket every subsequent kernel launch with CUDA events on the
+ * context's stream and accumulate its device time per kernel kind; 0 stops.
+ * Enabling also clears the accumulated totals.  Errors: ERR_ARG, ERR_CUDA. */
+int velopir_profile(velopir_ctx *ctx, int enable);
+
+/* Totals since profiling was enabled for one kernel kind: launches, work
+ * units (bootstraps for blind rotation, gates for key switch, ciphertexts
+ * for free gates) and device milliseconds.  Synchronises the stream.
+ * Errors: ERR_ARG, ERR_CUDA. */
+int velopir_profile_read(velopir_ctx *ctx, int kernel, uint64_t *launches, uint64_t *units, double *ms);
 
 /* ---- client side (host only; no GPU involved) --------------------------- */
 /* Key generation and encryption from caller-supplied random numbers (masks,

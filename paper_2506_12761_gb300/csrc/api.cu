@@ -37,7 +37,7 @@ struct velopir_ctx {
     size_t allocated = 0;   // bytes currently held
     std::string err;
     uint64_t launches = 0;
-    int path = VP_PATH_INT32_DENSE;
+    int path = VP_PATH_NTT;
     int big_rows = 1 << 16; // scratch capacity in extracted rows
 
     bool key_loaded = false;
@@ -50,6 +50,20 @@ struct velopir_ctx {
     uint64_t next_ticket = 1;
     size_t serve_reserved = 0;
     DevBuf s_br, s_ks, s_fr;   // serving-step job buffers
+
+    // tracing: events around each launch, resolved lazily
+    bool prof = false;
+    struct Rec { int kind; uint64_t units; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> spare;
+    uint64_t prof_launches[3] = {0, 0, 0}, prof_units[3] = {0, 0, 0};
+    double prof_ms[3] = {0, 0, 0};
+
+    // captured launch sequence of the last graph-mode program, replayed when
+    // the next one has the same launch list on the same buffers
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint64_t> graph_sig;
+    uint64_t graph_replays = 0;
 };
 
 namespace {
@@ -207,8 +221,7 @@ int launch_br(velopir_ctx *c, const BrJob *jobs, int n)
     return launch_br_dense(jobs, n, as<uint32_t>(c->bk), as<uint32_t>(c->big), as<int>(c->errw), c->stream);
 }
 
-// Upload the flattened jobs to (br, ks, fr) device buffers and issue every launch in order.
-int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+int upload(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
 {
     int rc;
     if ((rc = ensure(c, dbr, std::max<size_t>(1, F.br.size()) * sizeof(BrJob)))) return rc;
@@ -217,12 +230,98 @@ int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
     if (!F.br.empty()) CU(cudaMemcpyAsync(dbr.p, F.br.data(), F.br.size() * sizeof(BrJob), cudaMemcpyHostToDevice, c->stream));
     if (!F.ks.empty()) CU(cudaMemcpyAsync(dks.p, F.ks.data(), F.ks.size() * sizeof(KsJob), cudaMemcpyHostToDevice, c->stream));
     if (!F.fr.empty()) CU(cudaMemcpyAsync(dfr.p, F.fr.data(), F.fr.size() * sizeof(FreeJob), cudaMemcpyHostToDevice, c->stream));
+    return VELOPIR_OK;
+}
+
+int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr);
+
+// Upload the flattened jobs to (br, ks, fr) device buffers and issue every launch in order.
+int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+{
+    int rc;
+    if ((rc = upload(c, F, dbr, dks, dfr))) return rc;
+    return launches_only(c, F, dbr, dks, dfr);
+}
+
+// The launch sequence captured once into a CUDA graph and replayed; the job
+// lists are uploaded before each replay, so only the launch list (kinds,
+// offsets, sizes) and the buffers must match the captured one.
+int issue_graph(velopir_ctx *c, const Flat &F)
+{
+    int rc;
+    if ((rc = upload(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr))) return rc;
+    std::vector<uint64_t> sig;
+    sig.reserve(F.launches.size() * 3 + 8);
     for (const Launch &l : F.launches) {
+        sig.push_back((uint64_t)l.kind);
+        sig.push_back((uint64_t)l.off);
+        sig.push_back((uint64_t)l.n);
+    }
+    for (const DevBuf *b : {&c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->big, &c->bk, &c->bk_ntt, &c->ksk})
+        sig.push_back((uint64_t)(uintptr_t)b->p);
+    sig.push_back((uint64_t)c->path);
+    if (!c->graph_exec || sig != c->graph_sig) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        const bool prof = c->prof;
+        c->prof = false;
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = launches_only(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->prof = prof;
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return fail(c, VELOPIR_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, VELOPIR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->graph_sig.swap(sig);
+    } else {
+        c->graph_replays++;
+    }
+    CU(cudaGraphLaunch(c->graph_exec, c->stream));
+    return VELOPIR_OK;
+}
+
+int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+{
+    for (const Launch &l : F.launches) {
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (c->prof) {
+            for (cudaEvent_t *e : {&ea, &eb}) {
+                if (!c->spare.empty()) { *e = c->spare.back(); c->spare.pop_back(); }
+                else CU(cudaEventCreate(e));
+            }
+            CU(cudaEventRecord(ea, c->stream));
+        }
         if (l.kind == 0) c->launches += launch_br(c, as<BrJob>(dbr) + l.off, l.n);
         else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), c->stream);
         else c->launches += launch_free(as<FreeJob>(dfr) + l.off, l.n, c->stream);
         CU(cudaGetLastError());
+        if (c->prof) {
+            CU(cudaEventRecord(eb, c->stream));
+            c->recs.push_back({l.kind, (uint64_t)l.n, ea, eb});
+        }
     }
+    return VELOPIR_OK;
+}
+
+int prof_drain(velopir_ctx *c)
+{
+    if (c->recs.empty()) return VELOPIR_OK;
+    CU(cudaStreamSynchronize(c->stream));
+    for (auto &r : c->recs) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_launches[r.kind] += 1;
+        c->prof_units[r.kind] += r.units;
+        c->prof_ms[r.kind] += ms;
+        c->spare.push_back(r.a);
+        c->spare.push_back(r.b);
+    }
+    c->recs.clear();
     return VELOPIR_OK;
 }
 
@@ -239,7 +338,7 @@ int check_device_error(velopir_ctx *c)
 }
 
 // Run a whole program synchronously with the context's shared scratch.
-int run_program(velopir_ctx *c, Program &P)
+int run_program(velopir_ctx *c, Program &P, bool graph = false)
 {
     int rc;
     if ((rc = ensure_path_key(c))) return rc;
@@ -256,7 +355,9 @@ int run_program(velopir_ctx *c, Program &P)
         flatten_layer(L, cap, pool, P.phys, F);
         flatten_free(L.fr, pool, P.phys, F);
     }
-    if ((rc = issue(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr))) return rc;
+    if (graph) rc = issue_graph(c, F);
+    else rc = issue(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr);
+    if (rc) return rc;
     return check_device_error(c);
 }
 
@@ -329,6 +430,7 @@ int build_batch(velopir_ctx *c, int gate, const uint32_t *din, uint32_t *dout, s
 struct ServeQuery {
     uint64_t ticket = 0;
     velopir_query q{};
+    std::vector<uint32_t> db, payload;   // host copies of the plaintext database
     Program P;
     size_t cursor = 0;      // next layer
     bool pre_done = false;
@@ -549,6 +651,8 @@ int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void 
         CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
+    if (configure_br_dense() != 0 || configure_br_ntt() != 0)
+        return fail(nullptr, VELOPIR_ERR_CUDA, "cannot raise the shared-memory limit of the blind-rotation kernels");
     int rc = ensure(c, c->errw, 256);
     if (rc) { g_create_error = c->err; return rc; }
     CU(cudaMemsetAsync(c->errw.p, 0, 256, c->stream));
@@ -569,6 +673,9 @@ int velopir_destroy(velopir_ctx *c)
     DevBuf *bufs[] = {&c->bk, &c->ksk, &c->bk_ntt, &c->big, &c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->pool,
                       &c->in, &c->out, &c->errw, &c->s_br, &c->s_ks, &c->s_fr};
     for (DevBuf *b : bufs) dev_free(c, *b);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->spare) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return VELOPIR_OK;
@@ -648,11 +755,32 @@ int velopir_bootstrap_plain(velopir_ctx *c, velopir_gate gate, const uint32_t *l
     return bootstrap_common(c, gate, lwe_in, lwe_out, count, true);
 }
 
-static int run_query(velopir_ctx *c, const velopir_query &q)
+// The scheduler reads the plaintext database on the host: bring a
+// device-resident database or payload over first.
+static int host_plaintext(velopir_ctx *c, velopir_query &q, std::vector<uint32_t> &db, std::vector<uint32_t> &pay)
+{
+    const size_t dbw = q.kind == VP_QUERY_INTV ? 4 * q.D : q.D;
+    if (q.db && q.D && is_device_ptr(q.db)) {
+        db.resize(dbw);
+        CU(cudaMemcpy(db.data(), q.db, dbw * 4, cudaMemcpyDeviceToHost));
+        q.db = db.data();
+    }
+    if (q.payload && q.D && is_device_ptr(q.payload)) {
+        pay.resize(q.D);
+        CU(cudaMemcpy(pay.data(), q.payload, q.D * 4, cudaMemcpyDeviceToHost));
+        q.payload = pay.data();
+    }
+    return VELOPIR_OK;
+}
+
+static int run_query(velopir_ctx *c, velopir_query q)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
     int rc;
     if ((rc = validate_query(c, q))) return rc;
+    std::vector<uint32_t> hdb, hpay;
+    cudaSetDevice(c->device);
+    if ((rc = host_plaintext(c, q, hdb, hpay))) return rc;
     if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
     cudaSetDevice(c->device);
     if (q.D == 0) return VELOPIR_OK;
@@ -680,6 +808,61 @@ static int run_query(velopir_ctx *c, const velopir_query &q)
     if ((rc = run_program(c, P))) return rc;
     return finish_out(c, o);
 }
+
+int velopir_query_batch(velopir_ctx *c, const velopir_query *qs, size_t nq, int use_graph)
+{
+    if (!c || (!qs && nq)) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    cudaSetDevice(c->device);
+    int rc;
+    std::vector<velopir_query> q(qs, qs + nq);
+    std::vector<std::vector<uint32_t>> hdb(nq), hpay(nq);
+    size_t inw = 0, outw = 0;
+    for (size_t i = 0; i < nq; ++i) {
+        if ((rc = validate_query(c, q[i]))) return rc;
+        if ((rc = host_plaintext(c, q[i], hdb[i], hpay[i]))) return rc;
+        inw += query_in_words(q[i]);
+        if (!is_device_ptr(q[i].out)) outw += query_out_words(q[i]);
+    }
+    if ((rc = ensure(c, c->in, std::max<size_t>(1, inw) * 4))) return rc;
+    if ((rc = ensure(c, c->out, std::max<size_t>(1, outw) * 4))) return rc;
+    Program P;
+    Builder B(P);
+    std::vector<OutStage> outs(nq);
+    size_t ino = 0, outo = 0;
+    for (size_t i = 0; i < nq; ++i) {
+        const velopir_query &x = q[i];
+        if (x.D == 0) continue;
+        const uint32_t *da = nullptr, *db = nullptr;
+        if (x.kind == VP_QUERY_INTV) {
+            if ((rc = stage_in(c, x.enc_a, 32 * kLweWords, ino, &da))) return rc;
+            if ((rc = stage_in(c, x.enc_b, 32 * kLweWords, ino + 32 * kLweWords, &db))) return rc;
+        } else if ((rc = stage_in(c, x.enc_a, query_in_words(x), ino, &da))) {
+            return rc;
+        }
+        ino += query_in_words(x);
+        OutStage &o = outs[i];
+        o.user = x.out;
+        o.words = query_out_words(x);
+        o.host = !is_device_ptr(x.out);
+        o.dev = o.host ? as<uint32_t>(c->out) + outo : x.out;
+        if (o.host) outo += o.words;
+        std::vector<Ref> a(32), b(32);
+        const int na = x.kind == VP_QUERY_IDM ? x.id_bits : 32;
+        for (int k = 0; k < na; ++k) a[k] = B.input(da + (size_t)k * kLweWords);
+        if (x.kind == VP_QUERY_INTV)
+            for (int k = 0; k < 32; ++k) b[k] = B.input(db + (size_t)k * kLweWords);
+        if (x.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), x.db, x.D, o.dev);
+        else if (x.kind == VP_QUERY_COV) build_cov(B, a.data(), x.db, x.D, o.dev);
+        else build_idm(B, a.data(), x.id_bits, x.db, x.D, x.payload, x.payload_bits, o.dev);
+    }
+    if ((rc = run_program(c, P, use_graph != 0))) return rc;
+    for (auto &o : outs)
+        if (o.user && (rc = finish_out(c, o))) return rc;
+    return VELOPIR_OK;
+}
+
+uint64_t velopir_graph_replays(velopir_ctx *c) { return c ? c->graph_replays : 0; }
 
 int velopir_interval_query(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, const uint32_t *rects,
                            size_t D, uint32_t *out_bits)
@@ -730,8 +913,20 @@ int velopir_submit(velopir_ctx *c, const velopir_query *q, uint64_t *ticket)
     if (q->D == 0) return fail(c, VELOPIR_ERR_ARG, "empty database");
     if (c->waiting.size() >= 4096) return fail(c, VELOPIR_ERR_BUSY, "serving queue full");
     std::unique_ptr<ServeQuery> s(new ServeQuery());
-    s->ticket = c->next_ticket++;
     s->q = *q;
+    cudaSetDevice(c->device);
+    {
+        const size_t dbw = q->kind == VP_QUERY_INTV ? 4 * q->D : q->D;
+        s->db.resize(dbw);
+        CU(cudaMemcpy(s->db.data(), q->db, dbw * 4, cudaMemcpyDefault));
+        s->q.db = s->db.data();
+        if (q->payload) {
+            s->payload.resize(q->D);
+            CU(cudaMemcpy(s->payload.data(), q->payload, q->D * 4, cudaMemcpyDefault));
+            s->q.payload = s->payload.data();
+        }
+    }
+    s->ticket = c->next_ticket++;
     *ticket = s->ticket;
     c->waiting.push_back(std::move(s));
     return VELOPIR_OK;
@@ -786,5 +981,28 @@ int velopir_sync(velopir_ctx *c)
 const char *velopir_last_error(velopir_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 uint64_t velopir_launch_count(velopir_ctx *c) { return c ? c->launches : 0; }
+
+int velopir_profile(velopir_ctx *c, int enable)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    cudaSetDevice(c->device);
+    int rc = prof_drain(c);
+    if (rc) return rc;
+    for (int k = 0; k < 3; ++k) { c->prof_launches[k] = c->prof_units[k] = 0; c->prof_ms[k] = 0; }
+    c->prof = enable != 0;
+    return VELOPIR_OK;
+}
+
+int velopir_profile_read(velopir_ctx *c, int kernel, uint64_t *launches, uint64_t *units, double *ms)
+{
+    if (!c || kernel < 0 || kernel > 2 || !launches || !units || !ms) return fail(c, VELOPIR_ERR_ARG, "bad argument");
+    cudaSetDevice(c->device);
+    int rc = prof_drain(c);
+    if (rc) return rc;
+    *launches = c->prof_launches[kernel];
+    *units = c->prof_units[kernel];
+    *ms = c->prof_ms[kernel];
+    return VELOPIR_OK;
+}
 
 }  // extern "C"

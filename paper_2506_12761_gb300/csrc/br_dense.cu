@@ -56,19 +56,33 @@ __device__ __forceinline__ void load_bk_step(uint32_t *dst, const uint32_t *src,
         : "memory");
 }
 
-// Bounded wait on the mbarrier phase `parity`; records a timeout instead of hanging.
-__device__ __forceinline__ void mbar_wait(unsigned long long *bar, uint32_t parity, int *err)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait on the mbarrier phase `parity` for at most kWaitNs; on timeout record
+// it in the error word and return false.  Once any wait has given up, later
+// waits return at once, so a failed launch ends quickly instead of spinning.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *err)
+{
+    if (*reinterpret_cast<volatile int *>(err) != kDevOk) return false;
+    const uint64_t t0 = global_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
-        if (ok) return;
+        if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) {
+            atomicExch(err, kDevTimeout);
+            return false;
+        }
     }
-    atomicExch(err, kDevTimeout);
 }
 
 __device__ __forceinline__ int32_t sbyte(uint32_t w, int b) { return (int32_t)(int8_t)(w >> (8 * b)); }
@@ -221,6 +235,12 @@ br_dense_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__res
 }  // namespace
 
 int br_dense_jobs_per_cta() { return BT; }
+
+// Raise the dynamic shared-memory limit once per process (outside any stream capture).
+int configure_br_dense()
+{
+    return cudaFuncSetAttribute(br_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) == cudaSuccess ? 0 : -1;
+}
 
 int launch_br_dense(const BrJob *jobs, int njobs, const uint32_t *bk, uint32_t *big, int *err,
                     cudaStream_t st)

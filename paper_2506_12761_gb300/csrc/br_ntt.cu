@@ -1,9 +1,542 @@
-// Blind rotation with an exact two-prime number-theoretic transform (placeholder
-// until the transform kernels land; the path reports itself unavailable).
+// Blind rotation with the external product computed exactly by a two-prime
+// number-theoretic transform (integer pipe only; no floating point).
+//
+// Per step i the product out_j = sum_r D_r(X) * BK_i[r][j](X) mod (X^N+1) is an
+// integer polynomial whose coefficients are bounded by 6 * N * 64 * 2^32 <
+// 2^50.6 in magnitude (digits |d| <= 64, key words < 2^32).  It is computed
+// modulo p0 = 998244353 and p1 = 1004535809 (both 1 mod 2N, below 2^30) with
+// negacyclic NTTs, recombined by the Chinese remainder theorem into the exact
+// signed integer (p0 * p1 > 2^59.7), and reduced mod 2^32: bit-identical to
+// the dense contraction.
+//
+// Transform: Cooley-Tukey forward / Gentleman-Sande inverse with the powers of
+// a primitive 2N-th root psi in bit-reversed order (the merged negacyclic
+// form), Shoup multiplications with lazy reduction (values kept below 4p).
+// The pointwise products use Montgomery reduction against the transformed key
+// stored in Montgomery form with N^-1 folded in.
+//
+// Layout: one warp owns one bootstrap.  A 1024-point transform lives in the
+// warp's registers, 32 points per lane; the five stages whose pairs lie in
+// one lane run in registers, a padded 32x33 shared-memory transpose moves to
+// the other lane grouping, and five more stages run in registers.  No block
+// barrier is involved: each warp synchronises only itself.  A producer warp
+// streams each step's transformed key, one prime (48 KB) at a time, into a
+// double buffer with bulk asynchronous copies; full/empty mbarriers hand the
+// halves between producer and compute warps.
+#include <cstdio>
+#include <vector>
+
 #include "vp_internal.h"
 
 namespace vp {
-size_t bk_ntt_words() { return 0; }
-int prepare_bk_ntt(const uint32_t *, uint32_t *, cudaStream_t) { return 0; }
-int launch_br_ntt(const BrJob *, int, const uint32_t *, uint32_t *, int *, cudaStream_t) { return 0; }
+namespace {
+
+constexpr int WARPS = 6;                       // compute warps = bootstraps per CTA
+constexpr int THREADS = (WARPS + 1) * 32;      // + one producer warp
+constexpr uint32_t kP[2] = {998244353u, 1004535809u};
+constexpr int kXch = 32 * 33;                  // padded transpose tile
+constexpr size_t kHalfWords = (size_t)kRows * 2 * kN;   // one prime's transformed BK_i: 12288 words
+constexpr size_t kBkNttWords = (size_t)kn * 2 * kHalfWords;
+
+// Twiddles psi^(+-brv(k)) and their Shoup companions floor(w * 2^32 / p):
+// [prime][0 = forward, 1 = inverse][k].  Uniformly indexed stages read the
+// constant bank; lane-dependent stages read the global copy.
+__constant__ uint32_t cW[2][2][kN];
+__constant__ uint32_t cWs[2][2][kN];
+__device__ uint32_t gW[2][2][kN];
+__device__ uint32_t gWs[2][2][kN];
+
+struct PrimeConsts {
+    uint32_t p[2];
+    uint32_t pinv[2];        // -p^-1 mod 2^32 (Montgomery)
+    uint32_t scale[2];       // N^-1 * 2^32 mod p: folds the inverse scaling into the key
+    uint32_t crt_inv;        // p0^-1 mod p1
+    uint32_t crt_inv_s;      // its Shoup companion
+};
+__constant__ PrimeConsts cP;
+
+struct __align__(128) Smem {
+    uint32_t bkh[2][kHalfWords];          // 2 x 48 KB: this step's key, one prime per buffer
+    uint32_t acc[WARPS][2 * kN];          // 6 x 8 KB: ACC of each warp's bootstrap
+    uint32_t dig[WARPS][kRows * kN / 4];  // 6 x 6 KB: int8 digit polynomials, 4 per word
+    uint32_t xch[WARPS][kXch];            // 6 x 4.1 KB: transpose tiles
+    uint16_t abar[WARPS][kSlotWords];     // modulus-switched input
+    BrJob job[WARPS];
+    unsigned long long full[2], empty[2];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait on the mbarrier phase `parity` for at most kWaitNs; on timeout record
+// it in the error word and return false.  Once any wait has given up, later
+// waits return at once, so a failed launch ends quickly instead of spinning.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *err)
+{
+    if (*reinterpret_cast<volatile int *>(err) != kDevOk) return false;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) {
+            atomicExch(err, kDevTimeout);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the error word: used by the producer to let its
+// own copies land before the CTA exits.
+__device__ __forceinline__ void mbar_drain(unsigned long long *bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok || global_ns() - t0 > kWaitNs) return;
+    }
+}
+
+__device__ __forceinline__ void load_half(uint32_t *dst, const uint32_t *src, unsigned long long *bar)
+{
+    constexpr uint32_t bytes = kHalfWords * 4;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// x * w mod p in [0, 2p) for any x < 2^32 (Shoup, ws = floor(w 2^32 / p)).
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p)
+{
+    const uint32_t q = __umulhi(x, ws);
+    return x * w - q * p;
+}
+
+// Montgomery product x * b * 2^-32 mod p in [0, 2p) for x * b < p 2^32.
+__device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t b, uint32_t p, uint32_t pinv)
+{
+    const uint32_t lo = x * b, hi = __umulhi(x, b);
+    const uint32_t m = lo * pinv;
+    return hi + __umulhi(m, p) + (lo != 0u ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint32_t red2(uint32_t x, uint32_t m) { return min(x, x - m); }  // [0,2m) -> [0,m)
+
+// Cooley-Tukey butterfly, inputs and outputs below 4p.
+__device__ __forceinline__ void bf_fwd(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
+{
+    const uint32_t x = red2(X, 2 * p);
+    const uint32_t t = mul_shoup(Y, w, ws, p);
+    X = x + t;
+    Y = x - t + 2 * p;
+}
+
+// Gentleman-Sande butterfly, inputs and outputs below 2p.
+__device__ __forceinline__ void bf_inv(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
+{
+    const uint32_t x = X, y = Y;
+    X = red2(x + y, 2 * p);
+    Y = mul_shoup(x - y + 2 * p, w, ws, p);
+}
+
+// Lane L holds point L + 32t -> lane L holds point 32L + t.
+__device__ __forceinline__ void col_to_row(uint32_t (&x)[32], uint32_t *m, int lane)
+{
+#pragma unroll
+    for (int t = 0; t < 32; ++t) m[t * 33 + lane] = x[t];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) x[t] = m[lane * 33 + t];
+    __syncwarp();
+}
+
+// Lane L holds point 32L + t -> lane L holds point L + 32t.
+__device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int lane)
+{
+#pragma unroll
+    for (int t = 0; t < 32; ++t) m[lane * 33 + t] = x[t];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) x[t] = m[t * 33 + lane];
+    __syncwarp();
+}
+
+// Forward negacyclic NTT mod kP[pi] of one polynomial: column layout in,
+// row layout out (transform order), values below 4p.
+__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane)
+{
+    const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {            // distance 512 >> s: within a lane
+        const int dt = 16 >> s;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            if (t & dt) continue;
+            const int k = (1 << s) + (t >> (5 - s));
+            bf_fwd(x[t], x[t + dt], cW[pi][0][k], cWs[pi][0][k], p);
+        }
+    }
+    col_to_row(x, xch, lane);
+#pragma unroll
+    for (int s = 5; s < 10; ++s) {           // distance 512 >> s < 32: within a lane after the transpose
+        const int dt = 1 << (9 - s);
+        const int base = (1 << s) + (lane << (s - 5));
+#pragma unroll
+        for (int g = 0; g < (1 << (s - 5)); ++g) {
+            const uint32_t w = __ldg(&gW[pi][0][base + g]), ws = __ldg(&gWs[pi][0][base + g]);
+#pragma unroll
+            for (int u = 0; u < dt; ++u) {
+                const int t = g * 2 * dt + u;
+                bf_fwd(x[t], x[t + dt], w, ws, p);
+            }
+        }
+    }
+}
+
+// Inverse negacyclic NTT mod kP[pi] of two polynomials at once: row layout
+// (transform order) in, column layout out (natural order), values below 2p;
+// the N^-1 scaling is folded into the key.
+__device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&b)[32], int pi, uint32_t *xch, int lane)
+{
+    const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {            // distance 1 << k: within a lane
+        const int dt = 1 << k;
+        const int base = (512 >> k) + (lane << (4 - k));
+#pragma unroll
+        for (int g = 0; g < (16 >> k); ++g) {
+            const uint32_t w = __ldg(&gW[pi][1][base + g]), ws = __ldg(&gWs[pi][1][base + g]);
+#pragma unroll
+            for (int u = 0; u < dt; ++u) {
+                const int t = g * 2 * dt + u;
+                bf_inv(a[t], a[t + dt], w, ws, p);
+                bf_inv(b[t], b[t + dt], w, ws, p);
+            }
+        }
+    }
+    row_to_col(a, xch, lane);
+    row_to_col(b, xch, lane);
+#pragma unroll
+    for (int k = 5; k < 10; ++k) {           // distance 32 << (k-5): within a lane
+        const int dt = 1 << (k - 5);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            if (t & dt) continue;
+            const int idx = (512 >> k) + (t >> (k - 4));
+            const uint32_t w = cW[pi][1][idx], ws = cWs[pi][1][idx];
+            bf_inv(a[t], a[t + dt], w, ws, p);
+            bf_inv(b[t], b[t + dt], w, ws, p);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ bkhat,
+              uint32_t *__restrict__ big, int *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int job0 = blockIdx.x * WARPS;
+    const int nact = min(WARPS, njobs - job0);
+
+    if (tid < WARPS) {
+        BrJob j{};
+        if (tid < nact) j = jobs[job0 + tid];
+        S.job[tid] = j;
+    }
+    if (tid == 0) {
+        mbar_init(&S.full[0], 1);
+        mbar_init(&S.full[1], 1);
+        mbar_init(&S.empty[0], (uint32_t)nact);
+        mbar_init(&S.empty[1], (uint32_t)nact);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == WARPS) {
+        // Producer: stream BK^_i one prime at a time into the two buffers.
+        if (lane == 0) {
+            int issued[2] = {0, 0};
+            for (int i = 0; i < kn; ++i)
+                for (int h = 0; h < 2; ++h) {
+                    if (i > 0 && !mbar_wait(&S.empty[h], (uint32_t)((i - 1) & 1), err)) goto drain;
+                    load_half(S.bkh[h], bkhat + ((size_t)i * 2 + h) * kHalfWords, &S.full[h]);
+                    issued[h] = i + 1;
+                }
+        drain:
+            // every issued copy must land before this CTA's shared memory is released
+            for (int h = 0; h < 2; ++h)
+                if (issued[h] > 0) mbar_drain(&S.full[h], (uint32_t)((issued[h] - 1) & 1));
+        }
+        return;
+    }
+    if (warp >= nact) return;
+
+    const BrJob J = S.job[warp];
+    uint32_t *acc = S.acc[warp];
+    uint32_t *dig = S.dig[warp];
+    uint32_t *xch = S.xch[warp];
+    uint16_t *abar = S.abar[warp];
+
+    // Gate pre-combination and modulus switch.
+    for (int i = lane; i < kLweWords; i += 32) {
+        uint32_t c = (i == kn) ? J.cst : 0u;
+        if (J.in0) c += (uint32_t)J.s0 * J.in0[i];
+        if (J.in1) c += (uint32_t)J.s1 * J.in1[i];
+        abar[i] = (uint16_t)((c + (1u << 20)) >> 21);
+    }
+    __syncwarp();
+    // ACC = (0, X^{-bbar} v), v = mu * sum_j X^j
+    {
+        const uint32_t bbar = abar[kn];
+        for (int k = lane; k < kN; k += 32) {
+            const uint32_t u = ((uint32_t)k + bbar) & (kTwoN - 1);
+            acc[k] = 0u;
+            acc[kN + k] = (u < (uint32_t)kN) ? kMu : (0u - kMu);
+        }
+    }
+    __syncwarp();
+
+    constexpr uint32_t kOff = (1u << 31) + (1u << 24) + (1u << 17) + (1u << 10);
+    const uint32_t p0 = kP[0], p1 = kP[1];
+    const unsigned long long P = (unsigned long long)p0 * p1;
+    const unsigned long long Phalf = P >> 1;
+
+#pragma unroll 1
+    for (int i = 0; i < kn; ++i) {
+        const uint32_t ab = abar[i];
+        // Rotate, subtract, decompose into 6 int8 digit polynomials (row r = 2(p-1)+q).
+#pragma unroll 1
+        for (int u = 0; u < 8; ++u) {
+            const int k0 = 128 * u + 4 * lane;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint32_t *a = acc + q * kN;
+                const uint4 cur = *reinterpret_cast<const uint4 *>(a + k0);
+                const uint32_t cv[4] = {cur.x, cur.y, cur.z, cur.w};
+                uint32_t d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t src = ((uint32_t)(k0 + e) - ab) & (kTwoN - 1);
+                    uint32_t v = a[src & (kN - 1)];
+                    if (src >= (uint32_t)kN) v = 0u - v;
+                    const uint32_t y = v - cv[e] + kOff;
+                    d0 |= ((y >> 25) & 127u) << (8 * e);   // digit + 64, levels p = 1, 2, 3
+                    d1 |= ((y >> 18) & 127u) << (8 * e);
+                    d2 |= ((y >> 11) & 127u) << (8 * e);
+                }
+                dig[(0 * 2 + q) * (kN / 4) + k0 / 4] = d0;
+                dig[(1 * 2 + q) * (kN / 4) + k0 / 4] = d1;
+                dig[(2 * 2 + q) * (kN / 4) + k0 / 4] = d2;
+            }
+        }
+        __syncwarp();
+
+        uint32_t res0[32], res1[32];
+#pragma unroll 1
+        for (int pi = 0; pi < 2; ++pi) {
+            const uint32_t p = pi ? p1 : p0;
+            const uint32_t pinv = cP.pinv[pi];
+            mbar_wait(&S.full[pi], (uint32_t)(i & 1), err);
+            const uint32_t *bk = S.bkh[pi];
+            uint32_t a0[32], a1[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) { a0[t] = 0u; a1[t] = 0u; }
+#pragma unroll 1
+            for (int r = 0; r < kRows; ++r) {
+                uint32_t x[32];
+                const unsigned char *dr = reinterpret_cast<const unsigned char *>(dig + r * (kN / 4));
+#pragma unroll
+                for (int t = 0; t < 32; ++t) x[t] = (uint32_t)dr[lane + 32 * t] - 64u + p;   // digit mod p
+                ntt_fwd(x, pi, xch, lane);
+                const uint32_t *b0 = bk + (r * 2 + 0) * kN + lane;
+                const uint32_t *b1 = bk + (r * 2 + 1) * kN + lane;
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    a0[t] = red2(a0[t] + mul_mont(x[t], b0[32 * t], p, pinv), 2 * p);
+                    a1[t] = red2(a1[t] + mul_mont(x[t], b1[32 * t], p, pinv), 2 * p);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[pi]);
+            ntt_inv2(a0, a1, pi, xch, lane);
+            if (pi == 0) {
+#pragma unroll
+                for (int t = 0; t < 32; ++t) { res0[t] = red2(a0[t], p); res1[t] = red2(a1[t], p); }
+            } else {
+                // CRT: v = x0 + p0 * ((x1 - x0) p0^-1 mod p1), lifted to (-P/2, P/2], taken mod 2^32.
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int k = lane + 32 * t;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t x0 = j ? res1[t] : res0[t];
+                        const uint32_t x1 = red2(j ? a1[t] : a0[t], p1);
+                        const uint32_t tq = red2(mul_shoup(x1 - x0 + p1, cP.crt_inv, cP.crt_inv_s, p1), p1);
+                        const unsigned long long v = (unsigned long long)x0 + (unsigned long long)p0 * tq;
+                        const uint32_t lo = (uint32_t)v - (v > Phalf ? (uint32_t)P : 0u);
+                        acc[j * kN + k] += lo;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    // Sample extract: a'_0 = a_0, a'_j = -a_{N-j}, b' = b_0.
+    uint32_t *row = big + (size_t)J.big * kBigWords;
+    for (int k = lane; k < kN; k += 32) row[k == 0 ? 0 : kN - k] = k == 0 ? acc[0] : 0u - acc[k];
+    if (lane == 0) row[kN] = acc[kN];
+}
+
+// One warp per (step, prime, row, component): reduce the BK polynomial mod p,
+// transform it with the same forward NTT, fold N^-1 and the Montgomery factor,
+// and store it in the order the pointwise stage reads (index t*32 + lane for
+// transform point 32*lane + t).
+__global__ void __launch_bounds__(128) bk_ntt_kernel(const uint32_t *__restrict__ bk, uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t xch[4][kXch];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t id = (size_t)blockIdx.x * 4 + warp;       // ((i * 2 + pi) * 12 + rj)
+    if (id >= (size_t)kn * 2 * kRows * 2) return;
+    const int rj = (int)(id % (kRows * 2));
+    const int pi = (int)((id / (kRows * 2)) % 2);
+    const size_t i = id / (kRows * 2 * 2);
+    const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
+    const uint32_t *src = bk + (i * kRows * 2 + rj) * kN;
+    uint32_t x[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) x[t] = src[lane + 32 * t] % p;
+    ntt_fwd(x, pi, xch[warp], lane);
+    uint32_t *dst = out + id * kN;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        const uint32_t v = x[t] % p;
+        dst[t * 32 + lane] = (uint32_t)(((unsigned long long)v * cP.scale[pi]) % p);
+    }
+}
+
+uint32_t powmod(uint64_t b, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1;
+    b %= m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+int brv10(int k)
+{
+    int r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((k >> b) & 1) << (9 - b);
+    return r;
+}
+
+bool g_tables_ready[64] = {false};
+
+int upload_tables()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && g_tables_ready[dev]) return 0;
+    static uint32_t W[2][2][kN], Ws[2][2][kN];
+    PrimeConsts pc{};
+    for (int pi = 0; pi < 2; ++pi) {
+        const uint64_t p = kP[pi];
+        const uint32_t psi = powmod(3, (p - 1) / kTwoN, p);      // 3 generates Z_p^* for both primes
+        if (powmod(psi, kN, p) != p - 1) return -1;              // psi must be a primitive 2N-th root
+        const uint32_t ipsi = powmod(psi, p - 2, p);
+        for (int k = 0; k < kN; ++k) {
+            W[pi][0][k] = powmod(psi, brv10(k), p);
+            W[pi][1][k] = powmod(ipsi, brv10(k), p);
+            for (int d = 0; d < 2; ++d) Ws[pi][d][k] = (uint32_t)(((uint64_t)W[pi][d][k] << 32) / p);
+        }
+        uint32_t inv = 1;                                         // p^-1 mod 2^32 by Newton iteration
+        for (int it = 0; it < 5; ++it) inv *= 2u - (uint32_t)p * inv;
+        pc.p[pi] = (uint32_t)p;
+        pc.pinv[pi] = 0u - inv;
+        const uint64_t ninv = powmod(kN, p - 2, p);
+        const uint64_t r = ((uint64_t)1 << 32) % p;
+        pc.scale[pi] = (uint32_t)(ninv * r % p);
+    }
+    pc.crt_inv = powmod(kP[0], kP[1] - 2, kP[1]);
+    pc.crt_inv_s = (uint32_t)(((uint64_t)pc.crt_inv << 32) / kP[1]);
+    if (cudaMemcpyToSymbol(cW, W, sizeof W) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(cWs, Ws, sizeof Ws) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(gW, W, sizeof W) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(gWs, Ws, sizeof Ws) != cudaSuccess) return -1;
+    if (cudaMemcpyToSymbol(cP, &pc, sizeof pc) != cudaSuccess) return -1;
+    if (dev >= 0 && dev < 64) g_tables_ready[dev] = true;
+    return 0;
+}
+
+}  // namespace
+
+size_t bk_ntt_words() { return kBkNttWords; }
+
+int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st)
+{
+    if (upload_tables() != 0) return 0;
+    const size_t warps = (size_t)kn * 2 * kRows * 2;
+    bk_ntt_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(bk, bk_ntt);
+    return 1;
+}
+
+// Raise the dynamic shared-memory limit once per process (outside any stream capture).
+int configure_br_ntt()
+{
+    return cudaFuncSetAttribute(br_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) == cudaSuccess ? 0 : -1;
+}
+
+int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st)
+{
+    if (njobs <= 0) return 0;
+    static bool configured = false;
+    const int smem = (int)sizeof(Smem);
+    if (!configured) {
+        if (cudaFuncSetAttribute(br_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return 0;
+        configured = true;
+    }
+    const int grid = (njobs + WARPS - 1) / WARPS;
+    br_ntt_kernel<<<grid, THREADS, smem, st>>>(jobs, njobs, bk_ntt, big, err);
+    return 1;
+}
+
 }  // namespace vp

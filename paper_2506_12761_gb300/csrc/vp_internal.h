@@ -65,12 +65,15 @@ static_assert(sizeof(FreeJob) == 32, "FreeJob layout");
 
 // Device-side error codes written to the context's error word.
 enum : int { kDevOk = 0, kDevTimeout = 1 };
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of every device-side wait (2 s)
 
 // ---- kernel launchers (each returns the number of kernel launches issued) ----
 int launch_br_dense(const BrJob *jobs, int njobs, const uint32_t *bk, uint32_t *big, int *err,
                     cudaStream_t st);
 int br_dense_jobs_per_cta();
 
+int configure_br_dense();
+int configure_br_ntt();
 int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err,
                   cudaStream_t st);
 int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st);

@@ -33,7 +33,9 @@ EXPORTS = [
     "velopir_coordinate_query", "velopir_id_match", "velopir_submit", "velopir_poll",
     "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
+    "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
 ]
+VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
 
 
 class VelopirError(RuntimeError):
@@ -86,6 +88,11 @@ def lib() -> ctypes.CDLL:
             "velopir_client_keygen": (i, [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
             "velopir_client_encrypt_bits": (i, [vp, vp, vp, vp, sz, vp]),
             "velopir_client_decrypt_bits": (i, [vp, vp, sz, vp]),
+            "velopir_profile": (i, [vp, i]),
+            "velopir_query_batch": (i, [vp, ctypes.POINTER(Query), sz, i]),
+            "velopir_graph_replays": (u64, [vp]),
+            "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                         ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -154,6 +161,22 @@ def velopir_id_match(ctx, enc_id, id_bits: int, ids, D: int, payload, payload_bi
     _check(ctx, lib().velopir_id_match(ctx, ptr(enc_id), id_bits, ptr(ids), D, ptr(payload), payload_bits, ptr(out)))
 
 
+def velopir_query_batch(ctx, queries, use_graph: bool = False) -> None:
+    arr = (Query * len(queries))(*queries)
+    _check(ctx, lib().velopir_query_batch(ctx, arr, len(queries), int(use_graph)))
+
+
+def velopir_graph_replays(ctx) -> int:
+    return int(lib().velopir_graph_replays(ctx))
+
+
+def make_query(kind: int, enc_a, db, D: int, out, enc_b=None, id_bits: int = 0, payload=None,
+               payload_bits: int = 0) -> Query:
+    """A velopir_query record; the caller keeps every buffer alive until the query finishes."""
+    return Query(kind, id_bits, payload_bits if payload is not None else 0, 0, ptr(enc_a), ptr(enc_b), ptr(db),
+                 ptr(payload), D, ptr(out))
+
+
 def velopir_submit(ctx, query: Query) -> int:
     t = ctypes.c_uint64()
     _check(ctx, lib().velopir_submit(ctx, ctypes.byref(query), ctypes.byref(t)))
@@ -183,6 +206,17 @@ def velopir_last_error(ctx) -> str:
 
 def velopir_launch_count(ctx) -> int:
     return int(lib().velopir_launch_count(ctx))
+
+
+def velopir_profile(ctx, enable: bool) -> None:
+    _check(ctx, lib().velopir_profile(ctx, int(enable)))
+
+
+def velopir_profile_read(ctx, kernel: int) -> tuple[int, int, float]:
+    """(launches, units, device ms) accumulated for one kernel kind."""
+    n, u, ms = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(ctx, lib().velopir_profile_read(ctx, kernel, ctypes.byref(n), ctypes.byref(u), ctypes.byref(ms)))
+    return n.value, u.value, ms.value
 
 
 def velopir_client_keygen(km, params: Params | None = None):

@@ -15,6 +15,7 @@ def gpu_ctx():
         bk, ksk = vp.velopir_client_keygen(km)
         ctx = vp.Context(0)
         vp.velopir_load_cloud_key(ctx.h, bk, ksk)
+        vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
         _state.update(ctx=ctx, s=km.s.copy())
     return _state["ctx"], _state["s"]
 

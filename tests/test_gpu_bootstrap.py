@@ -9,7 +9,7 @@ from paper_2506_12761_gb300 import synth
 from paper_2506_12761_gb300 import velopir as vp
 
 pytestmark = pytest.mark.gpu
-PATHS = [vp.VP_PATH_INT32_DENSE]
+PATHS = [vp.VP_PATH_INT32_DENSE, vp.VP_PATH_NTT]
 
 
 def random_inputs(s, count, arity, seed):
@@ -55,9 +55,10 @@ def test_mux_and_device_buffers(path, paper_keys):
     assert np.array_equal(vp.velopir_client_decrypt_bits(s, out), np.where(bits[:, 0] == 1, bits[:, 1], bits[:, 2]))
 
 
-def test_plain_equals_batched(paper_keys):
+@pytest.mark.parametrize("path", PATHS)
+def test_plain_equals_batched(path, paper_keys):
     ctx, s = gpu_ctx()
-    vp.velopir_set_path(ctx.h, vp.VP_PATH_INT32_DENSE)
+    vp.velopir_set_path(ctx.h, path)
     inp, _ = random_inputs(s, 3, 2, seed=70)
     a = np.zeros((3, 631), dtype=np.uint32)
     b = np.zeros((3, 631), dtype=np.uint32)
@@ -76,12 +77,29 @@ def test_empty_and_bad_arguments():
         vp.velopir_set_path(ctx.h, 7)
 
 
-def test_trivial_inputs_take_no_rotation_steps(paper_keys):
+@pytest.mark.parametrize("path", PATHS)
+def test_trivial_inputs_take_no_rotation_steps(path, paper_keys):
     """A trivial input (zero mask) rotates by abar_i = 0 at every step."""
     ctx, s = gpu_ctx()
+    vp.velopir_set_path(ctx.h, path)
     inp = np.zeros((2, 2, 631), dtype=np.uint32)
     inp[0, :, 630] = 1 << 29
     inp[1, 0, 630] = (1 << 32) - (1 << 29)
     out = np.zeros((2, 631), dtype=np.uint32)
     vp.velopir_bootstrap_batch(ctx.h, vp.VP_AND, inp, out, 2)
     assert np.array_equal(out, oracle.gate_batch(paper_keys, oracle.AND, inp))
+
+
+def test_paths_agree_on_a_larger_batch():
+    """The dense and NTT paths give identical bits on a batch spanning many CTAs."""
+    ctx, s = gpu_ctx()
+    inp, bits = random_inputs(s, 157, 2, seed=80)
+    outs = []
+    for path in PATHS:
+        vp.velopir_set_path(ctx.h, path)
+        o = np.zeros((157, 631), dtype=np.uint32)
+        vp.velopir_bootstrap_batch(ctx.h, vp.VP_ORYN, inp, o, 157)
+        outs.append(o)
+    vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(vp.velopir_client_decrypt_bits(s, outs[1]), bits[:, 0] | (1 - bits[:, 1]))

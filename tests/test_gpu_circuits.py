@@ -75,3 +75,19 @@ def test_degenerate_shapes(paper_keys):
     assert np.array_equal(out, oracle.idm_payload(paper_keys, x, [3], [9], 4))
     # D = 0: nothing to do
     vp.velopir_id_match(ctx.h, x, 2, np.zeros(1, dtype=np.uint32), 0, None, 0, out)
+
+
+def test_device_resident_database(paper_keys):
+    """Ciphertexts, database and output all in device memory."""
+    import torch
+    ctx, s = gpu_ctx()
+    w = synth.intv_workload(2, substream=4)
+    cx = encrypt_value_bits(s, w["x"], 32, 507)
+    cy = encrypt_value_bits(s, w["y"], 32, 508)
+    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
+    dx, dy = (torch.from_numpy(a.view(np.int32)).cuda() for a in (cx, cy))
+    dr = torch.from_numpy(rects.view(np.int32)).cuda()
+    dout = torch.zeros((2, 631), dtype=torch.int32, device="cuda")
+    vp.velopir_interval_query(ctx.h, dx, dy, dr, 2, dout)
+    out = dout.cpu().numpy().view(np.uint32)
+    assert np.array_equal(out, oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))

@@ -1,0 +1,130 @@
+"""Multi-query batches (one merged program, optional CUDA-graph replay) and the
+continuous-batching serving loop: every result is bit-identical to the same
+query run alone, and to the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import encrypt_value_bits, gpu_ctx
+from paper_2506_12761_gb300 import synth
+from paper_2506_12761_gb300 import velopir as vp
+
+pytestmark = pytest.mark.gpu
+
+
+def make_queries(s, seed):
+    """IntV D=2, CoV D=3, IdM-8 D=4 with payload: three modes, uneven sizes."""
+    qs = []
+    w = synth.intv_workload(2, substream=seed)
+    cx, cy = encrypt_value_bits(s, w["x"], 32, 900 + seed), encrypt_value_bits(s, w["y"], 32, 901 + seed)
+    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
+    qs.append(dict(kind=vp.VP_QUERY_INTV, a=cx, b=cy, db=rects, D=2, out=np.zeros((2, 631), np.uint32)))
+    w = synth.cov_workload(3, substream=seed + 1)
+    cell = encrypt_value_bits(s, w["cell"], 32, 902 + seed)
+    qs.append(dict(kind=vp.VP_QUERY_COV, a=cell, db=w["cells"].astype(np.uint32), D=3, out=np.zeros((3, 631), np.uint32)))
+    w = synth.idm_workload(4, 8, payload=True, substream=seed + 2)
+    x = encrypt_value_bits(s, w["query"], 8, 903 + seed)
+    qs.append(dict(kind=vp.VP_QUERY_IDM, a=x, db=w["ids"].astype(np.uint32), D=4, id_bits=8,
+                   payload=w["payload"].astype(np.uint32), payload_bits=32, out=np.zeros((32, 631), np.uint32)))
+    return qs
+
+
+def as_record(q):
+    return vp.make_query(q["kind"], q["a"], q["db"], q["D"], q["out"], enc_b=q.get("b"), id_bits=q.get("id_bits", 0),
+                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0))
+
+
+def run_alone(ctx, q):
+    out = np.zeros_like(q["out"])
+    if q["kind"] == vp.VP_QUERY_INTV:
+        vp.velopir_interval_query(ctx.h, q["a"], q["b"], q["db"], q["D"], out)
+    elif q["kind"] == vp.VP_QUERY_COV:
+        vp.velopir_coordinate_query(ctx.h, q["a"], q["db"], q["D"], out)
+    else:
+        vp.velopir_id_match(ctx.h, q["a"], q["id_bits"], q["db"], q["D"], q["payload"], q["payload_bits"], out)
+    return out
+
+
+def test_query_batch_matches_alone_and_oracle(paper_keys):
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 1)
+    vp.velopir_query_batch(ctx.h, [as_record(q) for q in qs])
+    for q in qs:
+        assert np.array_equal(q["out"], run_alone(ctx, q))
+    intv, cov, idm = qs
+    assert np.array_equal(intv["out"], oracle.intv_batch(paper_keys, intv["a"], intv["b"], intv["db"].astype(np.uint64)))
+    assert np.array_equal(cov["out"], oracle.cov_batch(paper_keys, cov["a"], cov["db"]))
+    assert np.array_equal(idm["out"], oracle.idm_payload(paper_keys, idm["a"], idm["db"], idm["payload"], 32))
+
+
+def test_query_batch_graph_replay():
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 2)
+    r0 = vp.velopir_graph_replays(ctx.h)
+    vp.velopir_query_batch(ctx.h, [as_record(q) for q in qs], use_graph=True)
+    first = [q["out"].copy() for q in qs]
+    for q in qs:
+        q["out"][:] = 0
+    vp.velopir_query_batch(ctx.h, [as_record(q) for q in qs], use_graph=True)
+    assert vp.velopir_graph_replays(ctx.h) == r0 + 1
+    for q, f in zip(qs, first):
+        assert np.array_equal(q["out"], f)
+        assert np.array_equal(q["out"], run_alone(ctx, q))
+
+
+def test_serving_results_identical_alone_and_in_the_mix():
+    """Queries arriving while others are on the GPU are admitted into the
+    running layer batches; each result equals the query run alone."""
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 3) + make_queries(s, 4)
+    alone = [run_alone(ctx, q) for q in qs]
+    tickets = {}
+    pending = list(range(len(qs)))
+    done = set()
+    polls = 0
+    # staggered arrivals: one new query every other poll
+    while len(done) < len(qs):
+        if pending and polls % 2 == 0:
+            i = pending.pop(0)
+            tickets[i] = vp.velopir_submit(ctx.h, as_record(qs[i]))
+        for i, t in list(tickets.items()):
+            if i not in done and vp.velopir_poll(ctx.h, t):
+                done.add(i)
+        polls += 1
+        assert polls < 500
+    for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], a)
+    assert vp.velopir_queue_depth(ctx.h) == (0, 0)
+
+
+def test_serving_admission_respects_memory_budget():
+    """A context with a small HBM budget admits queries one at a time but still finishes them all."""
+    _, s = gpu_ctx()
+    from gpu_common import _state
+    km = synth.key_material()
+    bk, ksk = vp.velopir_client_keygen(km)
+    ctx = vp.Context(0, hbm_budget_bytes=700 << 20)
+    vp.velopir_load_cloud_key(ctx.h, bk, ksk)
+    qs = make_queries(s, 5)
+    alone = [run_alone(_state["ctx"], q) for q in qs]
+    ts = [vp.velopir_submit(ctx.h, as_record(q)) for q in qs]
+    left = set(range(len(qs)))
+    for _ in range(400):
+        for i in list(left):
+            if vp.velopir_poll(ctx.h, ts[i]):
+                left.discard(i)
+        if not left:
+            break
+    assert not left
+    for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], a)
+    ctx.close()
+
+
+def test_submit_errors():
+    ctx, s = gpu_ctx()
+    bad = vp.Query(7, 0, 0, 0, None, None, None, None, 1, None)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_submit(ctx.h, bad)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_poll(ctx.h, 10 ** 9)
