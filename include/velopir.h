@@ -117,6 +117,37 @@ int velopir_set_path(velopir_ctx *ctx, velopir_path path);
 int velopir_bootstrap_batch(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,
                             uint32_t *lwe_out, size_t count);
 
+/* Largest batch velopir_bootstrap_batch_noalloc accepts. */
+#define VELOPIR_NOALLOC_MAX_GATES 256
+
+/* velopir_bootstrap_batch for callers that cannot allocate device memory at
+ * call time: a serving process that reserved its HBM at start-up, code under
+ * a hard memory cap or behind a caching allocator that must not see foreign
+ * allocations, or a latency-critical loop where cudaMalloc/cudaFree (cudaFree
+ * synchronises the device) would stall other work.  The paper has no
+ * counterpart; this is a deployment variant of the same computation and
+ * returns bit-identical ciphertexts.
+ *
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Its scratch (job lists and extracted rows, 2.1 MB) is one file-scope device
+ * array of the library that every device loading the library holds until the
+ * process exits.  All calls share that array; calls whose GPU work overlaps
+ * race, so serialise them (one stream, or events).  Nothing in it needs
+ * clearing: each call writes every word it reads.
+ *   lwe_in, lwe_out: device memory, layouts as velopir_bootstrap_batch.
+ *   count: 0 .. VELOPIR_NOALLOC_MAX_GATES; larger counts return ERR_ARG.
+ * The context's key must be loaded (keys are allocated at load time, not
+ * here).  The selected path is used once its transformed key exists (after
+ * the context's first bootstrap or query on that path); before that the dense
+ * path runs; all paths give the same bits.
+ * The first call on a device performs a one-time set-up (it looks up the
+ * array's device address with that device current), so make that first call
+ * before any CUDA stream capture.  Synchronous: returns after the stream has
+ * finished the work.  Errors: ERR_ARG (sizes, null or host pointers, unknown
+ * gate), ERR_NOKEY, ERR_CUDA, ERR_TIMEOUT. */
+int velopir_bootstrap_batch_noalloc(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,
+                                    uint32_t *lwe_out, size_t count);
+
 /* The same gates issued one bootstrap per kernel launch (no batching): the
  * "plain" baseline against which batching is measured.  Same arguments. */
 int velopir_bootstrap_plain(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,

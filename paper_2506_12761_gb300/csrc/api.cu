@@ -625,6 +625,33 @@ int reap(velopir_ctx *c)
 
 }  // namespace
 
+// Internal accessors for entry points defined in other translation units.
+namespace vp {
+
+int ctx_resources(velopir_ctx *c, CtxResources *r)
+{
+    if (!c || !r) return VELOPIR_ERR_ARG;
+    r->device = c->device;
+    r->stream = c->stream;
+    r->key_loaded = c->key_loaded;
+    r->bk = as<uint32_t>(c->bk);
+    r->ksk = as<uint32_t>(c->ksk);
+    r->bk_ntt = (c->path == VP_PATH_NTT && c->bk_ntt_ready) ? as<uint32_t>(c->bk_ntt) : nullptr;
+    r->err = as<int>(c->errw);
+    return VELOPIR_OK;
+}
+
+int ctx_fail(velopir_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+
+int ctx_finish(velopir_ctx *c, uint64_t launches)
+{
+    c->launches += launches;
+    CU(cudaGetLastError());
+    return check_device_error(c);
+}
+
+}  // namespace vp
+
 // ================================ C ABI ====================================
 
 extern "C" {

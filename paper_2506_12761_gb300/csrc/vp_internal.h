@@ -84,4 +84,22 @@ int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const u
 int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st);
 int launch_pad_ksk(const uint32_t *ksk_abi, uint32_t *ksk_dev, cudaStream_t st);
 
+// What an entry point outside api.cu needs from a context.
+struct CtxResources {
+    int device;
+    cudaStream_t stream;
+    bool key_loaded;
+    const uint32_t *bk;       // dense-path key
+    const uint32_t *ksk;      // padded key-switching key
+    const uint32_t *bk_ntt;   // transformed key, or null if the NTT path is not selected and ready
+    int *err;                 // device error word
+};
+
+}  // namespace vp
+
+struct velopir_ctx;
+namespace vp {
+int ctx_resources(velopir_ctx *c, CtxResources *r);
+int ctx_fail(velopir_ctx *c, int code, const char *msg);
+int ctx_finish(velopir_ctx *c, uint64_t launches);   // count launches, sync, map the device error word
 }  // namespace vp

@@ -34,7 +34,9 @@ EXPORTS = [
     "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
+    "velopir_bootstrap_batch_noalloc",
 ]
+NOALLOC_MAX_GATES = 256
 VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
 
 
@@ -76,6 +78,7 @@ def lib() -> ctypes.CDLL:
             "velopir_set_path": (i, [vp, i]),
             "velopir_bootstrap_batch": (i, [vp, i, vp, vp, sz]),
             "velopir_bootstrap_plain": (i, [vp, i, vp, vp, sz]),
+            "velopir_bootstrap_batch_noalloc": (i, [vp, i, vp, vp, sz]),
             "velopir_interval_query": (i, [vp, vp, vp, vp, sz, vp]),
             "velopir_coordinate_query": (i, [vp, vp, vp, sz, vp]),
             "velopir_id_match": (i, [vp, vp, i, vp, sz, vp, i, vp]),
@@ -143,6 +146,11 @@ def velopir_set_path(ctx, path: int) -> None:
 
 def velopir_bootstrap_batch(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
     _check(ctx, lib().velopir_bootstrap_batch(ctx, gate, ptr(lwe_in), ptr(lwe_out), count))
+
+
+def velopir_bootstrap_batch_noalloc(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
+    """Allocation-free variant of velopir_bootstrap_batch (device buffers, count <= NOALLOC_MAX_GATES)."""
+    _check(ctx, lib().velopir_bootstrap_batch_noalloc(ctx, gate, ptr(lwe_in), ptr(lwe_out), count))
 
 
 def velopir_bootstrap_plain(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
