@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="dense", choices=["dense", "ntt"])
+    ap.add_argument("--path", default="ntt", choices=["dense", "ntt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     args = ap.parse_args()
@@ -212,6 +212,7 @@ def main():
     ctx = vp.Context(local, 0, stream.cuda_stream)
     vp.velopir_load_cloud_key(ctx.h, bk, ksk)
     vp.velopir_set_path(ctx.h, {"dense": vp.VP_PATH_INT32_DENSE, "ntt": vp.VP_PATH_NTT}[args.path])
+    waves = vp.velopir_autotune(ctx.h) if args.path == "ntt" else []   # tile-shape autotuner (untimed set-up)
     w = synth.intv_workload(D, substream=rank)
     cx = vp.velopir_client_encrypt_bits(km.s, synth.value_bits([w["x"]], 32)[0], synth.lwe_material(32, substream=1 + 2 * rank))
     cy = vp.velopir_client_encrypt_bits(km.s, synth.value_bits([w["y"]], 32)[0], synth.lwe_material(32, substream=2 + 2 * rank))
@@ -320,6 +321,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
                            "path": args.path, "parallelism": f"replicas x{world}",
+                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(range(4, 8), waves)),
+                                           "chosen": {n: vp.velopir_tuned_shape(ctx.h, n) for n in (1024, 2048, 4096)}},
                            "l2": "flushed between timed steps (256 MiB write, untimed)"},
                 "query_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
                 "plain": {"value": plain_rate, "unit": UNIT, "note": "one bootstrap per kernel launch, same kernels"},

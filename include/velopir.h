@@ -216,6 +216,19 @@ int velopir_query_batch(velopir_ctx *ctx, const velopir_query *queries, size_t n
 /* How many times a captured graph was replayed instead of re-captured. */
 uint64_t velopir_graph_replays(velopir_ctx *ctx);
 
+/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 4..7 for
+ * the NTT path).  Times one full wave of each shape on the device and keeps
+ * the results for this process; afterwards every launch of `count`
+ * bootstraps uses the shape with the fewest (waves x measured wave time), so
+ * uneven layer sizes waste fewer SMs.  wave_ms_out (nullable, n_out entries)
+ * receives the measured wave times in ms, shape 4 first.  A no-op on the
+ * dense path.  Errors: ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
+int velopir_autotune(velopir_ctx *ctx, double *wave_ms_out, int n_out);
+
+/* Bootstraps per CTA the current path would use for a batch of `count`
+ * (>= 1 on success).  Errors: ERR_ARG. */
+int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
+
 /* ---- serving: asynchronous queries with continuous batching ------------- */
 
 /* Enqueue a query.  It is admitted into the running batch as soon as the

@@ -891,6 +891,52 @@ int velopir_query_batch(velopir_ctx *c, const velopir_query *qs, size_t nq, int 
 
 uint64_t velopir_graph_replays(velopir_ctx *c) { return c ? c->graph_replays : 0; }
 
+int velopir_autotune(velopir_ctx *c, double *wave_ms_out, int n_out)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    cudaSetDevice(c->device);
+    int rc;
+    if ((rc = ensure_path_key(c))) return rc;
+    if (c->path != VP_PATH_NTT) return VELOPIR_OK;   // the dense path has one shape
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int wmax = ntt_warps_max(), wmin = ntt_warps_min();
+    const int njmax = sms * wmax;
+    if ((rc = ensure(c, c->big, (size_t)njmax * kBigWords * 4))) return rc;
+    if ((rc = ensure(c, c->jobs_br, (size_t)njmax * sizeof(BrJob)))) return rc;
+    // trivial inputs cost exactly as much as real ones: the kernels do not branch on data
+    std::vector<BrJob> jobs(njmax);
+    for (int j = 0; j < njmax; ++j) { jobs[j] = BrJob{}; jobs[j].big = j; }
+    CU(cudaMemcpyAsync(c->jobs_br.p, jobs.data(), jobs.size() * sizeof(BrJob), cudaMemcpyHostToDevice, c->stream));
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    for (int w = wmin; w <= wmax; ++w) {
+        float best = 0;
+        for (int rep = 0; rep < 3; ++rep) {
+            CU(cudaEventRecord(a, c->stream));
+            c->launches += launch_br_ntt_w(as<BrJob>(c->jobs_br), sms * w, as<uint32_t>(c->bk_ntt), as<uint32_t>(c->big),
+                                           as<int>(c->errw), c->stream, w);
+            CU(cudaEventRecord(b, c->stream));
+            CU(cudaEventSynchronize(b));
+            float ms = 0;
+            CU(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0 && (best == 0 || ms < best)) best = ms;   // rep 0 warms up
+        }
+        ntt_set_wave_ms(w, best);
+        if (wave_ms_out && w - wmin < n_out) wave_ms_out[w - wmin] = best;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return check_device_error(c);
+}
+
+int velopir_tuned_shape(velopir_ctx *c, size_t count)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    return c->path == VP_PATH_NTT ? ntt_pick_warps((int)std::min<size_t>(count, 1u << 30)) : br_dense_jobs_per_cta();
+}
+
 int velopir_interval_query(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, const uint32_t *rects,
                            size_t D, uint32_t *out_bits)
 {

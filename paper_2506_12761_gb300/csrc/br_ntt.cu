@@ -12,8 +12,8 @@
 // Transform: Cooley-Tukey forward / Gentleman-Sande inverse with the powers of
 // a primitive 2N-th root psi in bit-reversed order (the merged negacyclic
 // form), Shoup multiplications with lazy reduction (values kept below 4p).
-// The pointwise products use Montgomery reduction against the transformed key
-// stored in Montgomery form with N^-1 folded in.
+// The pointwise products are Shoup multiplications by the transformed key,
+// stored with N^-1 folded in and with each value's Shoup companion.
 //
 // Layout: one warp owns one bootstrap.  A 1024-point transform lives in the
 // warp's registers, 32 points per lane; the five stages whose pairs lie in
@@ -31,12 +31,13 @@
 namespace vp {
 namespace {
 
-constexpr int WARPS = 6;                       // compute warps = bootstraps per CTA
-constexpr int THREADS = (WARPS + 1) * 32;      // + one producer warp
+constexpr int kMaxWarps = 7;                   // compute warps = bootstraps per CTA (4..7, chosen per launch)
 constexpr uint32_t kP[2] = {998244353u, 1004535809u};
 constexpr int kXch = 32 * 33;                  // padded transpose tile
-constexpr size_t kHalfWords = (size_t)kRows * 2 * kN;   // one prime's transformed BK_i: 12288 words
-constexpr size_t kBkNttWords = (size_t)kn * 2 * kHalfWords;
+constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
+constexpr int kChunks = kn * 2 * kRows;        // consumed in this order: step, prime, row
+constexpr size_t kBkNttWords = (size_t)kChunks * kChunkWords;
+constexpr int kRing = 2;                       // ring slots of the key stream
 
 // Twiddles psi^(+-brv(k)) and their Shoup companions floor(w * 2^32 / p):
 // [prime][0 = forward, 1 = inverse][k].  Uniformly indexed stages read the
@@ -48,21 +49,21 @@ __device__ uint32_t gWs[2][2][kN];
 
 struct PrimeConsts {
     uint32_t p[2];
-    uint32_t pinv[2];        // -p^-1 mod 2^32 (Montgomery)
-    uint32_t scale[2];       // N^-1 * 2^32 mod p: folds the inverse scaling into the key
+    uint32_t scale[2];       // N^-1 mod p: folds the inverse scaling into the key
     uint32_t crt_inv;        // p0^-1 mod p1
     uint32_t crt_inv_s;      // its Shoup companion
 };
 __constant__ PrimeConsts cP;
 
-struct __align__(128) Smem {
-    uint32_t bkh[2][kHalfWords];          // 2 x 48 KB: this step's key, one prime per buffer
-    uint32_t acc[WARPS][2 * kN];          // 6 x 8 KB: ACC of each warp's bootstrap
-    uint32_t dig[WARPS][kRows * kN / 4];  // 6 x 6 KB: int8 digit polynomials, 4 per word
-    uint32_t xch[WARPS][kXch];            // 6 x 4.1 KB: transpose tiles
+template <int WARPS> struct __align__(128) Smem {
+    uint32_t ring[kRing][kChunkWords];    // 2 x 16 KB: stream of the transformed key
+    uint32_t acc[WARPS][2 * kN];          // 8 KB per warp: ACC of its bootstrap
+    uint32_t res[WARPS][2 * kN];          // 8 KB per warp: the product mod p0, held for the CRT
+    uint32_t dig[WARPS][kRows * kN / 4];  // 6 KB per warp: digit polynomials (digit + 64), one byte each
+    uint32_t xch[WARPS][kXch];            // 4.1 KB per warp: transpose tile
     uint16_t abar[WARPS][kSlotWords];     // modulus-switched input
     BrJob job[WARPS];
-    unsigned long long full[2], empty[2];
+    unsigned long long full[kRing], empty[kRing];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -125,9 +126,9 @@ __device__ __forceinline__ void mbar_drain(unsigned long long *bar, uint32_t par
     }
 }
 
-__device__ __forceinline__ void load_half(uint32_t *dst, const uint32_t *src, unsigned long long *bar)
+__device__ __forceinline__ void load_chunk(uint32_t *dst, const uint32_t *src, unsigned long long *bar)
 {
-    constexpr uint32_t bytes = kHalfWords * 4;
+    constexpr uint32_t bytes = kChunkWords * 4;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
     asm volatile(
@@ -142,14 +143,6 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 {
     const uint32_t q = __umulhi(x, ws);
     return x * w - q * p;
-}
-
-// Montgomery product x * b * 2^-32 mod p in [0, 2p) for x * b < p 2^32.
-__device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t b, uint32_t p, uint32_t pinv)
-{
-    const uint32_t lo = x * b, hi = __umulhi(x, b);
-    const uint32_t m = lo * pinv;
-    return hi + __umulhi(m, p) + (lo != 0u ? 1u : 0u);
 }
 
 __device__ __forceinline__ uint32_t red2(uint32_t x, uint32_t m) { return min(x, x - m); }  // [0,2m) -> [0,m)
@@ -194,33 +187,35 @@ __device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int l
 }
 
 // Forward negacyclic NTT mod kP[pi] of one polynomial: column layout in,
-// row layout out (transform order), values below 4p.
+// row layout out (transform order), values below 4p.  Every loop has a
+// compile-time trip count and every array index is a compile-time constant,
+// so the 32 points stay in registers.
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
+    const uint32_t *cw = &cW[pi][0][0], *cws = &cWs[pi][0][0];
 #pragma unroll
     for (int s = 0; s < 5; ++s) {            // distance 512 >> s: within a lane
         const int dt = 16 >> s;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            if (t & dt) continue;
+        for (int b = 0; b < 16; ++b) {
+            const int t = (b / dt) * 2 * dt + (b % dt);
             const int k = (1 << s) + (t >> (5 - s));
-            bf_fwd(x[t], x[t + dt], cW[pi][0][k], cWs[pi][0][k], p);
+            bf_fwd(x[t], x[t + dt], cw[k], cws[k], p);
         }
     }
     col_to_row(x, xch, lane);
+    const uint32_t *gw = &gW[pi][0][0], *gws = &gWs[pi][0][0];
 #pragma unroll
     for (int s = 5; s < 10; ++s) {           // distance 512 >> s < 32: within a lane after the transpose
         const int dt = 1 << (9 - s);
         const int base = (1 << s) + (lane << (s - 5));
 #pragma unroll
-        for (int g = 0; g < (1 << (s - 5)); ++g) {
-            const uint32_t w = __ldg(&gW[pi][0][base + g]), ws = __ldg(&gWs[pi][0][base + g]);
-#pragma unroll
-            for (int u = 0; u < dt; ++u) {
-                const int t = g * 2 * dt + u;
-                bf_fwd(x[t], x[t + dt], w, ws, p);
-            }
+        for (int b = 0; b < 16; ++b) {
+            const int g = b / dt;                                  // group of this lane's points
+            const int t = g * 2 * dt + (b % dt);
+            const uint32_t w = __ldg(gw + base + g), ws = __ldg(gws + base + g);
+            bf_fwd(x[t], x[t + dt], w, ws, p);
         }
     }
 }
@@ -228,46 +223,46 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
 // Inverse negacyclic NTT mod kP[pi] of two polynomials at once: row layout
 // (transform order) in, column layout out (natural order), values below 2p;
 // the N^-1 scaling is folded into the key.
-__device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&b)[32], int pi, uint32_t *xch, int lane)
+__device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], int pi, uint32_t *xch, int lane)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
+    const uint32_t *gw = &gW[pi][1][0], *gws = &gWs[pi][1][0];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {            // distance 1 << k: within a lane
         const int dt = 1 << k;
         const int base = (512 >> k) + (lane << (4 - k));
 #pragma unroll
-        for (int g = 0; g < (16 >> k); ++g) {
-            const uint32_t w = __ldg(&gW[pi][1][base + g]), ws = __ldg(&gWs[pi][1][base + g]);
-#pragma unroll
-            for (int u = 0; u < dt; ++u) {
-                const int t = g * 2 * dt + u;
-                bf_inv(a[t], a[t + dt], w, ws, p);
-                bf_inv(b[t], b[t + dt], w, ws, p);
-            }
+        for (int b = 0; b < 16; ++b) {
+            const int g = b / dt;
+            const int t = g * 2 * dt + (b % dt);
+            const uint32_t w = __ldg(gw + base + g), ws = __ldg(gws + base + g);
+            bf_inv(a[t], a[t + dt], w, ws, p);
+            bf_inv(c[t], c[t + dt], w, ws, p);
         }
     }
     row_to_col(a, xch, lane);
-    row_to_col(b, xch, lane);
+    row_to_col(c, xch, lane);
+    const uint32_t *cw = &cW[pi][1][0], *cws = &cWs[pi][1][0];
 #pragma unroll
     for (int k = 5; k < 10; ++k) {           // distance 32 << (k-5): within a lane
         const int dt = 1 << (k - 5);
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            if (t & dt) continue;
+        for (int b = 0; b < 16; ++b) {
+            const int t = (b / dt) * 2 * dt + (b % dt);
             const int idx = (512 >> k) + (t >> (k - 4));
-            const uint32_t w = cW[pi][1][idx], ws = cWs[pi][1][idx];
-            bf_inv(a[t], a[t + dt], w, ws, p);
-            bf_inv(b[t], b[t + dt], w, ws, p);
+            bf_inv(a[t], a[t + dt], cw[idx], cws[idx], p);
+            bf_inv(c[t], c[t + dt], cw[idx], cws[idx], p);
         }
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+template <int WARPS>
+__global__ void __launch_bounds__((WARPS + 1) * 32, 1)
 br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ bkhat,
               uint32_t *__restrict__ big, int *err)
 {
     extern __shared__ unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<WARPS> &S = *reinterpret_cast<Smem<WARPS> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int job0 = blockIdx.x * WARPS;
     const int nact = min(WARPS, njobs - job0);
@@ -278,28 +273,29 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
         S.job[tid] = j;
     }
     if (tid == 0) {
-        mbar_init(&S.full[0], 1);
-        mbar_init(&S.full[1], 1);
-        mbar_init(&S.empty[0], (uint32_t)nact);
-        mbar_init(&S.empty[1], (uint32_t)nact);
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&S.full[r], 1);
+            mbar_init(&S.empty[r], (uint32_t)nact);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (warp == WARPS) {
-        // Producer: stream BK^_i one prime at a time into the two buffers.
+        // Producer: stream the transformed key chunk by chunk (step, prime,
+        // row) through the ring; a slot is refilled once every compute warp
+        // has released its previous chunk.
         if (lane == 0) {
-            int issued[2] = {0, 0};
-            for (int i = 0; i < kn; ++i)
-                for (int h = 0; h < 2; ++h) {
-                    if (i > 0 && !mbar_wait(&S.empty[h], (uint32_t)((i - 1) & 1), err)) goto drain;
-                    load_half(S.bkh[h], bkhat + ((size_t)i * 2 + h) * kHalfWords, &S.full[h]);
-                    issued[h] = i + 1;
-                }
-        drain:
+            int issued = 0;
+            for (int c = 0; c < kChunks; ++c) {
+                const int slot = c % kRing;
+                if (c >= kRing && !mbar_wait(&S.empty[slot], (uint32_t)((c / kRing - 1) & 1), err)) break;
+                load_chunk(S.ring[slot], bkhat + (size_t)c * kChunkWords, &S.full[slot]);
+                issued = c + 1;
+            }
             // every issued copy must land before this CTA's shared memory is released
-            for (int h = 0; h < 2; ++h)
-                if (issued[h] > 0) mbar_drain(&S.full[h], (uint32_t)((issued[h] - 1) & 1));
+            for (int c = (issued > kRing ? issued - kRing : 0); c < issued; ++c)
+                mbar_drain(&S.full[c % kRing], (uint32_t)((c / kRing) & 1));
         }
         return;
     }
@@ -307,6 +303,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
 
     const BrJob J = S.job[warp];
     uint32_t *acc = S.acc[warp];
+    uint32_t *res = S.res[warp];
     uint32_t *dig = S.dig[warp];
     uint32_t *xch = S.xch[warp];
     uint16_t *abar = S.abar[warp];
@@ -338,40 +335,31 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
 #pragma unroll 1
     for (int i = 0; i < kn; ++i) {
         const uint32_t ab = abar[i];
-        // Rotate, subtract, decompose into 6 int8 digit polynomials (row r = 2(p-1)+q).
-#pragma unroll 1
-        for (int u = 0; u < 8; ++u) {
-            const int k0 = 128 * u + 4 * lane;
+        // Rotate, subtract, decompose into 6 digit polynomials (row r = 2(p-1)+q),
+        // stored as digit + 64 in one byte; lanes take consecutive coefficients.
+        {
+            unsigned char *d8 = reinterpret_cast<unsigned char *>(dig);
+#pragma unroll 2
+            for (int m = 0; m < 32; ++m) {
+                const int k = lane + 32 * m;
+                const uint32_t src = ((uint32_t)k - ab) & (kTwoN - 1);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const uint32_t *a = acc + q * kN;
-                const uint4 cur = *reinterpret_cast<const uint4 *>(a + k0);
-                const uint32_t cv[4] = {cur.x, cur.y, cur.z, cur.w};
-                uint32_t d0 = 0, d1 = 0, d2 = 0;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const uint32_t src = ((uint32_t)(k0 + e) - ab) & (kTwoN - 1);
+                for (int q = 0; q < 2; ++q) {
+                    const uint32_t *a = acc + q * kN;
                     uint32_t v = a[src & (kN - 1)];
                     if (src >= (uint32_t)kN) v = 0u - v;
-                    const uint32_t y = v - cv[e] + kOff;
-                    d0 |= ((y >> 25) & 127u) << (8 * e);   // digit + 64, levels p = 1, 2, 3
-                    d1 |= ((y >> 18) & 127u) << (8 * e);
-                    d2 |= ((y >> 11) & 127u) << (8 * e);
+                    const uint32_t y = v - a[k] + kOff;
+                    d8[(0 * 2 + q) * kN + k] = (unsigned char)((y >> 25) & 127u);
+                    d8[(1 * 2 + q) * kN + k] = (unsigned char)((y >> 18) & 127u);
+                    d8[(2 * 2 + q) * kN + k] = (unsigned char)((y >> 11) & 127u);
                 }
-                dig[(0 * 2 + q) * (kN / 4) + k0 / 4] = d0;
-                dig[(1 * 2 + q) * (kN / 4) + k0 / 4] = d1;
-                dig[(2 * 2 + q) * (kN / 4) + k0 / 4] = d2;
             }
         }
         __syncwarp();
 
-        uint32_t res0[32], res1[32];
 #pragma unroll 1
         for (int pi = 0; pi < 2; ++pi) {
             const uint32_t p = pi ? p1 : p0;
-            const uint32_t pinv = cP.pinv[pi];
-            mbar_wait(&S.full[pi], (uint32_t)(i & 1), err);
-            const uint32_t *bk = S.bkh[pi];
             uint32_t a0[32], a1[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) { a0[t] = 0u; a1[t] = 0u; }
@@ -382,20 +370,25 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
 #pragma unroll
                 for (int t = 0; t < 32; ++t) x[t] = (uint32_t)dr[lane + 32 * t] - 64u + p;   // digit mod p
                 ntt_fwd(x, pi, xch, lane);
-                const uint32_t *b0 = bk + (r * 2 + 0) * kN + lane;
-                const uint32_t *b1 = bk + (r * 2 + 1) * kN + lane;
+                const int c = (i * 2 + pi) * kRows + r;               // chunk of the key stream
+                const int slot = c % kRing;
+                mbar_wait(&S.full[slot], (uint32_t)((c / kRing) & 1), err);
+                const uint32_t *b0 = S.ring[slot] + lane;   // [w0 | w0' | w1 | w1'], 1024 words each
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
-                    a0[t] = red2(a0[t] + mul_mont(x[t], b0[32 * t], p, pinv), 2 * p);
-                    a1[t] = red2(a1[t] + mul_mont(x[t], b1[32 * t], p, pinv), 2 * p);
+                    a0[t] = red2(a0[t] + mul_shoup(x[t], b0[32 * t], b0[kN + 32 * t], p), 2 * p);
+                    a1[t] = red2(a1[t] + mul_shoup(x[t], b0[2 * kN + 32 * t], b0[3 * kN + 32 * t], p), 2 * p);
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.empty[slot]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.empty[pi]);
             ntt_inv2(a0, a1, pi, xch, lane);
             if (pi == 0) {
 #pragma unroll
-                for (int t = 0; t < 32; ++t) { res0[t] = red2(a0[t], p); res1[t] = red2(a1[t], p); }
+                for (int t = 0; t < 32; ++t) {
+                    res[lane + 32 * t] = red2(a0[t], p);
+                    res[kN + lane + 32 * t] = red2(a1[t], p);
+                }
             } else {
                 // CRT: v = x0 + p0 * ((x1 - x0) p0^-1 mod p1), lifted to (-P/2, P/2], taken mod 2^32.
 #pragma unroll
@@ -403,7 +396,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
                     const int k = lane + 32 * t;
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const uint32_t x0 = j ? res1[t] : res0[t];
+                        const uint32_t x0 = res[j * kN + k];
                         const uint32_t x1 = red2(j ? a1[t] : a0[t], p1);
                         const uint32_t tq = red2(mul_shoup(x1 - x0 + p1, cP.crt_inv, cP.crt_inv_s, p1), p1);
                         const unsigned long long v = (unsigned long long)x0 + (unsigned long long)p0 * tq;
@@ -423,29 +416,32 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
 }
 
 // One warp per (step, prime, row, component): reduce the BK polynomial mod p,
-// transform it with the same forward NTT, fold N^-1 and the Montgomery factor,
-// and store it in the order the pointwise stage reads (index t*32 + lane for
-// transform point 32*lane + t).
+// transform it with the same forward NTT, fold N^-1, and store the values and
+// their Shoup companions in the order the pointwise stage reads (index
+// t*32 + lane for transform point 32*lane + t) inside the chunk of its
+// (step, prime, row).
 __global__ void __launch_bounds__(128) bk_ntt_kernel(const uint32_t *__restrict__ bk, uint32_t *__restrict__ out)
 {
     __shared__ uint32_t xch[4][kXch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t id = (size_t)blockIdx.x * 4 + warp;       // ((i * 2 + pi) * 12 + rj)
-    if (id >= (size_t)kn * 2 * kRows * 2) return;
-    const int rj = (int)(id % (kRows * 2));
-    const int pi = (int)((id / (kRows * 2)) % 2);
-    const size_t i = id / (kRows * 2 * 2);
+    const size_t id = (size_t)blockIdx.x * 4 + warp;       // ((i * 2 + pi) * 6 + r) * 2 + j
+    if (id >= (size_t)kChunks * 2) return;
+    const int j = (int)(id % 2);
+    const int r = (int)((id / 2) % kRows);
+    const int pi = (int)((id / (2 * kRows)) % 2);
+    const size_t i = id / (2 * kRows * 2);
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
-    const uint32_t *src = bk + (i * kRows * 2 + rj) * kN;
+    const uint32_t *src = bk + ((i * kRows + r) * 2 + j) * kN;
     uint32_t x[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) x[t] = src[lane + 32 * t] % p;
     ntt_fwd(x, pi, xch[warp], lane);
-    uint32_t *dst = out + id * kN;
+    uint32_t *dst = out + (id / 2) * kChunkWords + (size_t)j * 2 * kN;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
-        const uint32_t v = x[t] % p;
-        dst[t * 32 + lane] = (uint32_t)(((unsigned long long)v * cP.scale[pi]) % p);
+        const uint32_t v = (uint32_t)(((unsigned long long)(x[t] % p) * cP.scale[pi]) % p);
+        dst[t * 32 + lane] = v;
+        dst[kN + t * 32 + lane] = (uint32_t)(((unsigned long long)v << 32) / p);
     }
 }
 
@@ -487,13 +483,8 @@ int upload_tables()
             W[pi][1][k] = powmod(ipsi, brv10(k), p);
             for (int d = 0; d < 2; ++d) Ws[pi][d][k] = (uint32_t)(((uint64_t)W[pi][d][k] << 32) / p);
         }
-        uint32_t inv = 1;                                         // p^-1 mod 2^32 by Newton iteration
-        for (int it = 0; it < 5; ++it) inv *= 2u - (uint32_t)p * inv;
         pc.p[pi] = (uint32_t)p;
-        pc.pinv[pi] = 0u - inv;
-        const uint64_t ninv = powmod(kN, p - 2, p);
-        const uint64_t r = ((uint64_t)1 << 32) % p;
-        pc.scale[pi] = (uint32_t)(ninv * r % p);
+        pc.scale[pi] = powmod(kN, p - 2, p);
     }
     pc.crt_inv = powmod(kP[0], kP[1] - 2, kP[1]);
     pc.crt_inv_s = (uint32_t)(((uint64_t)pc.crt_inv << 32) / kP[1]);
@@ -506,6 +497,23 @@ int upload_tables()
     return 0;
 }
 
+template <int W> int configure_w()
+{
+    return cudaFuncSetAttribute(br_ntt_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(Smem<W>)) == cudaSuccess ? 0 : -1;
+}
+
+template <int W> void launch_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err,
+                               cudaStream_t st)
+{
+    br_ntt_kernel<W><<<(njobs + W - 1) / W, (W + 1) * 32, sizeof(Smem<W>), st>>>(jobs, njobs, bk_ntt, big, err);
+}
+
+// Tuned per-wave time of each variant (ms for one full wave of 152 CTAs);
+// zero until velopir's autotuner has measured it.
+float g_wave_ms[kMaxWarps + 1] = {0};
+int g_sms = 0;
+
 }  // namespace
 
 size_t bk_ntt_words() { return kBkNttWords; }
@@ -513,7 +521,7 @@ size_t bk_ntt_words() { return kBkNttWords; }
 int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st)
 {
     if (upload_tables() != 0) return 0;
-    const size_t warps = (size_t)kn * 2 * kRows * 2;
+    const size_t warps = (size_t)kChunks * 2;
     bk_ntt_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(bk, bk_ntt);
     return 1;
 }
@@ -521,22 +529,48 @@ int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st)
 // Raise the dynamic shared-memory limit once per process (outside any stream capture).
 int configure_br_ntt()
 {
-    return cudaFuncSetAttribute(br_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) == cudaSuccess ? 0 : -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    return (configure_w<4>() | configure_w<5>() | configure_w<6>() | configure_w<7>()) ? -1 : 0;
+}
+
+int ntt_warps_min() { return 4; }
+int ntt_warps_max() { return kMaxWarps; }
+void ntt_set_wave_ms(int warps, float ms) { if (warps >= 4 && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
+
+// Bootstraps per CTA for a launch of njobs: the variant with the smallest
+// (waves x tuned wave time); without tuning, the largest CTA.
+int ntt_pick_warps(int njobs)
+{
+    int best = kMaxWarps;
+    double best_t = 0;
+    const int sms = g_sms > 0 ? g_sms : 152;
+    for (int w = 4; w <= kMaxWarps; ++w) {
+        if (g_wave_ms[w] <= 0) return kMaxWarps;
+        const int ctas = (njobs + w - 1) / w;
+        const double t = (double)((ctas + sms - 1) / sms) * g_wave_ms[w];
+        if (w == 4 || t < best_t) { best = w; best_t = t; }
+    }
+    return best;
+}
+
+int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st,
+                    int warps)
+{
+    if (njobs <= 0) return 0;
+    switch (warps) {
+    case 4: launch_w<4>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 5: launch_w<5>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 6: launch_w<6>(jobs, njobs, bk_ntt, big, err, st); break;
+    default: launch_w<7>(jobs, njobs, bk_ntt, big, err, st); break;
+    }
+    return 1;
 }
 
 int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st)
 {
-    if (njobs <= 0) return 0;
-    static bool configured = false;
-    const int smem = (int)sizeof(Smem);
-    if (!configured) {
-        if (cudaFuncSetAttribute(br_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return 0;
-        configured = true;
-    }
-    const int grid = (njobs + WARPS - 1) / WARPS;
-    br_ntt_kernel<<<grid, THREADS, smem, st>>>(jobs, njobs, bk_ntt, big, err);
-    return 1;
+    return launch_br_ntt_w(jobs, njobs, bk_ntt, big, err, st, ntt_pick_warps(njobs));
 }
 
 }  // namespace vp

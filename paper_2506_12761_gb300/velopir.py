@@ -34,7 +34,7 @@ EXPORTS = [
     "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
-    "velopir_bootstrap_batch_noalloc",
+    "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape",
 ]
 NOALLOC_MAX_GATES = 256
 VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
             "velopir_profile": (i, [vp, i]),
             "velopir_query_batch": (i, [vp, ctypes.POINTER(Query), sz, i]),
             "velopir_graph_replays": (u64, [vp]),
+            "velopir_autotune": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
+            "velopir_tuned_shape": (i, [vp, sz]),
             "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(ctypes.c_double)]),
         }
@@ -176,6 +178,20 @@ def velopir_query_batch(ctx, queries, use_graph: bool = False) -> None:
 
 def velopir_graph_replays(ctx) -> int:
     return int(lib().velopir_graph_replays(ctx))
+
+
+def velopir_autotune(ctx) -> list[float]:
+    """Measured full-wave times (ms) of the blind-rotation shapes, 4 bootstraps per CTA first."""
+    out = (ctypes.c_double * 8)()
+    _check(ctx, lib().velopir_autotune(ctx, out, 8))
+    return [x for x in out if x > 0]
+
+
+def velopir_tuned_shape(ctx, count: int) -> int:
+    rc = lib().velopir_tuned_shape(ctx, count)
+    if rc < 0:
+        _check(ctx, rc)
+    return rc
 
 
 def make_query(kind: int, enc_a, db, D: int, out, enc_b=None, id_bits: int = 0, payload=None,

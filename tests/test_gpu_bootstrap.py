@@ -103,3 +103,19 @@ def test_paths_agree_on_a_larger_batch():
     vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(vp.velopir_client_decrypt_bits(s, outs[1]), bits[:, 0] | (1 - bits[:, 1]))
+
+
+def test_autotuned_shapes_keep_parity(paper_keys):
+    """After the autotuner has timed every tile shape, batches of sizes that
+    favour different shapes still match the oracle bit for bit."""
+    ctx, s = gpu_ctx()
+    vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
+    waves = vp.velopir_autotune(ctx.h)
+    assert len(waves) == 4 and all(w > 0 for w in waves)
+    shapes = {vp.velopir_tuned_shape(ctx.h, n) for n in (152 * 4, 152 * 5, 152 * 6, 152 * 7, 1000, 4096)}
+    assert shapes <= {4, 5, 6, 7}
+    for count, seed in ((13, 90), (29, 91)):
+        inp, _ = random_inputs(s, count, 2, seed=seed)
+        out = np.zeros((count, 631), dtype=np.uint32)
+        vp.velopir_bootstrap_batch(ctx.h, vp.VP_NAND, inp, out, count)
+        assert np.array_equal(out, oracle.gate_batch(paper_keys, oracle.NAND, inp))
