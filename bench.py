@@ -107,14 +107,17 @@ def measured_peaks():
         return {}
 
 
-def traffic_for(kernel_src: str, units_per_launch: float):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this exact kernel source."""
+def traffic_for(kernel_src: str):
+    """DRAM bytes per launch (read + write) of the dominant kernel from the
+    committed ncu summary, if it was captured on this exact kernel source;
+    null otherwise.  The key dominates and is read once per launch, so the
+    figure does not scale with the bootstraps a launch processes."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         src = open(os.path.join(ROOT, "paper_2506_12761_gb300", "csrc", kernel_src), "rb").read()
         ent = rec.get(kernel_src)
         if ent and ent.get("sha256") == hashlib.sha256(src).hexdigest():
-            return ent["dram_bytes_per_unit"] * units_per_launch
+            return ent["dram_bytes_per_launch"]
     except Exception:
         pass
     return None
@@ -303,7 +306,7 @@ def main():
         peak = 152 * 64 * sm_max * 1e6 / 1e12
         unit = "T int32-multiply ops/s"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic_for(kernel_src, u_br / max(1, n_br)),
+                "traffic": traffic_for(kernel_src),
                 "kernel": kernel_src.replace(".cu", ""), "launches": n_br, "avg_launch_ms": ms_br / max(1, n_br),
                 "peak_basis": "152 SMs x 64 int32 multiply lanes/clk x max SM clock %.0f MHz" % sm_max,
                 "key_switch": {"launches": n_ks, "avg_launch_ms": ms_ks / max(1, n_ks),
@@ -321,7 +324,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
                            "path": args.path, "parallelism": f"replicas x{world}",
-                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(range(4, 8), waves)),
+                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(range(5, 11), waves)),
                                            "chosen": {n: vp.velopir_tuned_shape(ctx.h, n) for n in (1024, 2048, 4096)}},
                            "l2": "flushed between timed steps (256 MiB write, untimed)"},
                 "query_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},

@@ -216,12 +216,12 @@ int velopir_query_batch(velopir_ctx *ctx, const velopir_query *queries, size_t n
 /* How many times a captured graph was replayed instead of re-captured. */
 uint64_t velopir_graph_replays(velopir_ctx *ctx);
 
-/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 4..7 for
+/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 5..10 for
  * the NTT path).  Times one full wave of each shape on the device and keeps
  * the results for this process; afterwards every launch of `count`
  * bootstraps uses the shape with the fewest (waves x measured wave time), so
  * uneven layer sizes waste fewer SMs.  wave_ms_out (nullable, n_out entries)
- * receives the measured wave times in ms, shape 4 first.  A no-op on the
+ * receives the measured wave times in ms, shape 5 first.  A no-op on the
  * dense path.  Errors: ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
 int velopir_autotune(velopir_ctx *ctx, double *wave_ms_out, int n_out);
 
@@ -242,6 +242,13 @@ int velopir_submit(velopir_ctx *ctx, const velopir_query *q, uint64_t *ticket);
  * whether `ticket` has finished (*done = 1; its result is in q->out).
  * Errors: ERR_ARG (unknown ticket), ERR_CUDA, ERR_TIMEOUT. */
 int velopir_poll(velopir_ctx *ctx, uint64_t ticket, int *done);
+
+/* Advance the serving loop by at most one merged layer launch (admitting
+ * waiting queries first) and report up to `cap` tickets that have finished
+ * since the last report (*ndone of them, written to done[]).  A ticket
+ * reported here is not reported again by velopir_poll.  Errors: ERR_ARG,
+ * ERR_CUDA, ERR_TIMEOUT. */
+int velopir_progress(velopir_ctx *ctx, uint64_t *done, size_t cap, size_t *ndone);
 
 /* Number of admitted and waiting queries.  Errors: ERR_ARG. */
 int velopir_queue_depth(velopir_ctx *ctx, size_t *admitted, size_t *waiting);

@@ -1035,6 +1035,25 @@ int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
     return VELOPIR_OK;
 }
 
+int velopir_progress(velopir_ctx *c, uint64_t *done, size_t cap, size_t *ndone)
+{
+    if (!c || !ndone || (!done && cap)) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    cudaSetDevice(c->device);
+    *ndone = 0;
+    int rc;
+    if (!c->waiting.empty() || !c->active.empty()) {
+        if ((rc = serve_step(c))) return rc;
+        for (auto &s : c->active)
+            if (s->ev) cudaEventSynchronize(s->ev);
+        if ((rc = reap(c))) return rc;
+    }
+    while (!c->finished.empty() && *ndone < cap) {
+        done[(*ndone)++] = c->finished.front()->ticket;
+        c->finished.erase(c->finished.begin());
+    }
+    return VELOPIR_OK;
+}
+
 int velopir_queue_depth(velopir_ctx *c, size_t *admitted, size_t *waiting)
 {
     if (!c || !admitted || !waiting) return fail(c, VELOPIR_ERR_ARG, "null argument");

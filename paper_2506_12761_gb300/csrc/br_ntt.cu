@@ -31,7 +31,9 @@
 namespace vp {
 namespace {
 
-constexpr int kMaxWarps = 7;                   // compute warps = bootstraps per CTA (4..7, chosen per launch)
+constexpr int kMinWarps = 5;                   // compute warps = bootstraps per CTA (5..10, chosen per launch)
+constexpr int kMaxWarps = 10;
+constexpr uint32_t kTmemCols = 256;            // per CTA: up to 3 warps share a 32-lane quarter, 64 columns each
 constexpr uint32_t kP[2] = {998244353u, 1004535809u};
 constexpr int kXch = 32 * 33;                  // padded transpose tile
 constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
@@ -58,12 +60,12 @@ __constant__ PrimeConsts cP;
 template <int WARPS> struct __align__(128) Smem {
     uint32_t ring[kRing][kChunkWords];    // 2 x 16 KB: stream of the transformed key
     uint32_t acc[WARPS][2 * kN];          // 8 KB per warp: ACC of its bootstrap
-    uint32_t res[WARPS][2 * kN];          // 8 KB per warp: the product mod p0, held for the CRT
     uint32_t dig[WARPS][kRows * kN / 4];  // 6 KB per warp: digit polynomials (digit + 64), one byte each
     uint32_t xch[WARPS][kXch];            // 4.1 KB per warp: transpose tile
     uint16_t abar[WARPS][kSlotWords];     // modulus-switched input
     BrJob job[WARPS];
     unsigned long long full[kRing], empty[kRing];
+    uint32_t tmem_base;                   // Tensor Memory holding each warp's product mod p0
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -136,6 +138,34 @@ __device__ __forceinline__ void load_chunk(uint32_t *dst, const uint32_t *src, u
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Tensor Memory as per-lane scratch: a warp reaches only the 32 lanes of
+// quarter (warp id mod 4); each thread reads and writes its own lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // x * w mod p in [0, 2p) for any x < 2^32 (Shoup, ws = floor(w 2^32 / p)).
@@ -279,7 +309,15 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {   // warp 0 allocates the CTA's Tensor Memory and frees it at the end
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (warp == WARPS) {
         // Producer: stream the transformed key chunk by chunk (step, prime,
@@ -303,8 +341,9 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
 
     const BrJob J = S.job[warp];
     uint32_t *acc = S.acc[warp];
-    uint32_t *res = S.res[warp];
     uint32_t *dig = S.dig[warp];
+    // this warp's 64 columns in its lane quarter: [0, 32) component a, [32, 64) component b
+    const uint32_t tres = S.tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
     uint32_t *xch = S.xch[warp];
     uint16_t *abar = S.abar[warp];
 
@@ -385,18 +424,20 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
             ntt_inv2(a0, a1, pi, xch, lane);
             if (pi == 0) {
 #pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    res[lane + 32 * t] = red2(a0[t], p);
-                    res[kN + lane + 32 * t] = red2(a1[t], p);
-                }
+                for (int t = 0; t < 32; ++t) { a0[t] = red2(a0[t], p); a1[t] = red2(a1[t], p); }
+                tmem_st32(tres, a0);
+                tmem_st32(tres + 32, a1);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             } else {
                 // CRT: v = x0 + p0 * ((x1 - x0) p0^-1 mod p1), lifted to (-P/2, P/2], taken mod 2^32.
 #pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const int k = lane + 32 * t;
+                for (int j = 0; j < 2; ++j) {
+                    uint32_t x0v[32];
+                    tmem_ld32(tres + 32 * j, x0v);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const uint32_t x0 = res[j * kN + k];
+                    for (int t = 0; t < 32; ++t) {
+                        const int k = lane + 32 * t;
+                        const uint32_t x0 = x0v[t];
                         const uint32_t x1 = red2(j ? a1[t] : a0[t], p1);
                         const uint32_t tq = red2(mul_shoup(x1 - x0 + p1, cP.crt_inv, cP.crt_inv_s, p1), p1);
                         const unsigned long long v = (unsigned long long)x0 + (unsigned long long)p0 * tq;
@@ -413,6 +454,15 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
     uint32_t *row = big + (size_t)J.big * kBigWords;
     for (int k = lane; k < kN; k += 32) row[k == 0 ? 0 : kN - k] = k == 0 ? acc[0] : 0u - acc[k];
     if (lane == 0) row[kN] = acc[kN];
+
+    // All active compute warps are done with Tensor Memory: warp 0 frees it.
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(nact * 32) : "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
 }
 
 // One warp per (step, prime, row, component): reduce the BK polynomial mod p,
@@ -512,6 +562,7 @@ template <int W> void launch_w(const BrJob *jobs, int njobs, const uint32_t *bk_
 // Tuned per-wave time of each variant (ms for one full wave of 152 CTAs);
 // zero until velopir's autotuner has measured it.
 float g_wave_ms[kMaxWarps + 1] = {0};
+static_assert(sizeof(Smem<kMaxWarps>) <= 232448, "shared memory per CTA");
 int g_sms = 0;
 
 }  // namespace
@@ -532,12 +583,13 @@ int configure_br_ntt()
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    return (configure_w<4>() | configure_w<5>() | configure_w<6>() | configure_w<7>()) ? -1 : 0;
+    return (configure_w<5>() | configure_w<6>() | configure_w<7>() | configure_w<8>() | configure_w<9>() |
+            configure_w<10>()) ? -1 : 0;
 }
 
-int ntt_warps_min() { return 4; }
+int ntt_warps_min() { return kMinWarps; }
 int ntt_warps_max() { return kMaxWarps; }
-void ntt_set_wave_ms(int warps, float ms) { if (warps >= 4 && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
+void ntt_set_wave_ms(int warps, float ms) { if (warps >= kMinWarps && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
 
 // Bootstraps per CTA for a launch of njobs: the variant with the smallest
 // (waves x tuned wave time); without tuning, the largest CTA.
@@ -546,11 +598,11 @@ int ntt_pick_warps(int njobs)
     int best = kMaxWarps;
     double best_t = 0;
     const int sms = g_sms > 0 ? g_sms : 152;
-    for (int w = 4; w <= kMaxWarps; ++w) {
+    for (int w = kMinWarps; w <= kMaxWarps; ++w) {
         if (g_wave_ms[w] <= 0) return kMaxWarps;
         const int ctas = (njobs + w - 1) / w;
         const double t = (double)((ctas + sms - 1) / sms) * g_wave_ms[w];
-        if (w == 4 || t < best_t) { best = w; best_t = t; }
+        if (w == kMinWarps || t < best_t) { best = w; best_t = t; }
     }
     return best;
 }
@@ -560,10 +612,12 @@ int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32
 {
     if (njobs <= 0) return 0;
     switch (warps) {
-    case 4: launch_w<4>(jobs, njobs, bk_ntt, big, err, st); break;
     case 5: launch_w<5>(jobs, njobs, bk_ntt, big, err, st); break;
     case 6: launch_w<6>(jobs, njobs, bk_ntt, big, err, st); break;
-    default: launch_w<7>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 7: launch_w<7>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 8: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 9: launch_w<9>(jobs, njobs, bk_ntt, big, err, st); break;
+    default: launch_w<10>(jobs, njobs, bk_ntt, big, err, st); break;
     }
     return 1;
 }

@@ -34,7 +34,7 @@ EXPORTS = [
     "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
-    "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape",
+    "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
 ]
 NOALLOC_MAX_GATES = 256
 VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "velopir_submit": (i, [vp, ctypes.POINTER(Query), ctypes.POINTER(u64)]),
             "velopir_poll": (i, [vp, u64, ctypes.POINTER(i)]),
             "velopir_queue_depth": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+            "velopir_progress": (i, [vp, ctypes.POINTER(u64), sz, ctypes.POINTER(sz)]),
             "velopir_sync": (i, [vp]),
             "velopir_last_error": (ctypes.c_char_p, [vp]),
             "velopir_launch_count": (u64, [vp]),
@@ -181,7 +182,7 @@ def velopir_graph_replays(ctx) -> int:
 
 
 def velopir_autotune(ctx) -> list[float]:
-    """Measured full-wave times (ms) of the blind-rotation shapes, 4 bootstraps per CTA first."""
+    """Measured full-wave times (ms) of the blind-rotation shapes, 5 bootstraps per CTA first."""
     out = (ctypes.c_double * 8)()
     _check(ctx, lib().velopir_autotune(ctx, out, 8))
     return [x for x in out if x > 0]
@@ -211,6 +212,14 @@ def velopir_poll(ctx, ticket: int) -> bool:
     d = ctypes.c_int()
     _check(ctx, lib().velopir_poll(ctx, ticket, ctypes.byref(d)))
     return bool(d.value)
+
+
+def velopir_progress(ctx, cap: int = 256) -> list[int]:
+    """One serving step; the tickets that finished since the last report."""
+    buf = (ctypes.c_uint64 * cap)()
+    n = ctypes.c_size_t()
+    _check(ctx, lib().velopir_progress(ctx, buf, cap, ctypes.byref(n)))
+    return [int(buf[i]) for i in range(n.value)]
 
 
 def velopir_queue_depth(ctx) -> tuple[int, int]:
