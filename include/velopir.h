@@ -216,7 +216,7 @@ int velopir_query_batch(velopir_ctx *ctx, const velopir_query *queries, size_t n
 /* How many times a captured graph was replayed instead of re-captured. */
 uint64_t velopir_graph_replays(velopir_ctx *ctx);
 
-/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 5..10 for
+/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 5..8 for
  * the NTT path).  Times one full wave of each shape on the device and keeps
  * the results for this process; afterwards every launch of `count`
  * bootstraps uses the shape with the fewest (waves x measured wave time), so
@@ -262,6 +262,13 @@ const char *velopir_last_error(velopir_ctx *ctx);
 
 /* Kernel launches this context has issued since creation (for launch counting). */
 uint64_t velopir_launch_count(velopir_ctx *ctx);
+
+/* Failure-detection self-test: launches the library's bounded device wait on
+ * a barrier nothing ever completes.  The wait gives up after its time limit
+ * (2 s), the kernel returns normally, and the call returns
+ * VELOPIR_ERR_TIMEOUT; the context stays usable (the error word is cleared).
+ * Returns VELOPIR_OK only if the wait did not time out, which is a defect. */
+int velopir_selftest_wait_timeout(velopir_ctx *ctx);
 
 /* ---- tracing: per-kernel device time -------------------------------------- */
 

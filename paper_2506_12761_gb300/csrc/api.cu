@@ -1074,6 +1074,15 @@ const char *velopir_last_error(velopir_ctx *c) { return c ? c->err.c_str() : g_c
 
 uint64_t velopir_launch_count(velopir_ctx *c) { return c ? c->launches : 0; }
 
+int velopir_selftest_wait_timeout(velopir_ctx *c)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    cudaSetDevice(c->device);
+    c->launches += launch_wait_selftest(as<int>(c->errw), c->stream);
+    CU(cudaGetLastError());
+    return check_device_error(c);
+}
+
 int velopir_profile(velopir_ctx *c, int enable)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");

@@ -232,7 +232,24 @@ br_dense_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__res
     }
 }
 
+// Diagnostic: the bounded wait of the blind-rotation kernels on a barrier
+// nothing ever arrives at.  It gives up after kWaitNs, records kDevTimeout in
+// the error word and the kernel returns normally.
+__global__ void wait_selftest_kernel(int *err)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    mbar_wait(&bar, 0u, err);
+}
+
 }  // namespace
+
+int launch_wait_selftest(int *err, cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(err);
+    return 1;
+}
 
 int br_dense_jobs_per_cta() { return BT; }
 

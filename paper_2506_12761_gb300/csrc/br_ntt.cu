@@ -31,9 +31,10 @@
 namespace vp {
 namespace {
 
-constexpr int kMinWarps = 5;                   // compute warps = bootstraps per CTA (5..10, chosen per launch)
-constexpr int kMaxWarps = 10;
-constexpr uint32_t kTmemCols = 256;            // per CTA: up to 3 warps share a 32-lane quarter, 64 columns each
+constexpr int kMinWarps = 5;                   // compute warps = bootstraps per CTA (5..8, chosen per launch)
+constexpr int kMaxWarps = 8;
+constexpr int kTwLane = 31 * 32;               // lane-dependent twiddles of one transform: 31 groups x 32 lanes
+constexpr uint32_t kTmemCols = 256;            // per CTA: up to 2 warps share a 32-lane quarter, 64 columns each
 constexpr uint32_t kP[2] = {998244353u, 1004535809u};
 constexpr int kXch = 32 * 33;                  // padded transpose tile
 constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
@@ -48,6 +49,10 @@ __constant__ uint32_t cW[2][2][kN];
 __constant__ uint32_t cWs[2][2][kN];
 __device__ uint32_t gW[2][2][kN];
 __device__ uint32_t gWs[2][2][kN];
+// The lane-dependent twiddles of the in-lane stages after (forward) or before
+// (inverse) the transpose, as (w, w') pairs in [stage][group][lane] order so
+// that a warp reads them from shared memory without bank conflicts.
+__device__ uint2 gWL[2][2][kTwLane];
 
 struct PrimeConsts {
     uint32_t p[2];
@@ -59,6 +64,7 @@ __constant__ PrimeConsts cP;
 
 template <int WARPS> struct __align__(128) Smem {
     uint32_t ring[kRing][kChunkWords];    // 2 x 16 KB: stream of the transformed key
+    uint2 twl[2][2][kTwLane];             // 31 KB: lane-dependent twiddles [prime][direction]
     uint32_t acc[WARPS][2 * kN];          // 8 KB per warp: ACC of its bootstrap
     uint32_t dig[WARPS][kRows * kN / 4];  // 6 KB per warp: digit polynomials (digit + 64), one byte each
     uint32_t xch[WARPS][kXch];            // 4.1 KB per warp: transpose tile
@@ -177,10 +183,12 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 
 __device__ __forceinline__ uint32_t red2(uint32_t x, uint32_t m) { return min(x, x - m); }  // [0,2m) -> [0,m)
 
-// Cooley-Tukey butterfly, inputs and outputs below 4p.
+// Cooley-Tukey butterfly, inputs and outputs below 4p (inputs below 2p when
+// kReduced, which skips the reduction of X).
+template <bool kReduced = false>
 __device__ __forceinline__ void bf_fwd(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
 {
-    const uint32_t x = red2(X, 2 * p);
+    const uint32_t x = kReduced ? X : red2(X, 2 * p);
     const uint32_t t = mul_shoup(Y, w, ws, p);
     X = x + t;
     Y = x - t + 2 * p;
@@ -220,7 +228,7 @@ __device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int l
 // row layout out (transform order), values below 4p.  Every loop has a
 // compile-time trip count and every array index is a compile-time constant,
 // so the 32 points stay in registers.
-__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane)
+__device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane, const uint2 *twl)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
     const uint32_t *cw = &cW[pi][0][0], *cws = &cWs[pi][0][0];
@@ -231,21 +239,21 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
         for (int b = 0; b < 16; ++b) {
             const int t = (b / dt) * 2 * dt + (b % dt);
             const int k = (1 << s) + (t >> (5 - s));
-            bf_fwd(x[t], x[t + dt], cw[k], cws[k], p);
+            if (s == 0) bf_fwd<true>(x[t], x[t + dt], cw[k], cws[k], p);   // inputs are below 2p
+            else bf_fwd(x[t], x[t + dt], cw[k], cws[k], p);
         }
     }
     col_to_row(x, xch, lane);
-    const uint32_t *gw = &gW[pi][0][0], *gws = &gWs[pi][0][0];
 #pragma unroll
     for (int s = 5; s < 10; ++s) {           // distance 512 >> s < 32: within a lane after the transpose
         const int dt = 1 << (9 - s);
-        const int base = (1 << s) + (lane << (s - 5));
+        const int base = 32 * ((1 << (s - 5)) - 1);              // groups of the earlier stages
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
             const int g = b / dt;                                  // group of this lane's points
             const int t = g * 2 * dt + (b % dt);
-            const uint32_t w = __ldg(gw + base + g), ws = __ldg(gws + base + g);
-            bf_fwd(x[t], x[t + dt], w, ws, p);
+            const uint2 w = twl[base + g * 32 + lane];
+            bf_fwd(x[t], x[t + dt], w.x, w.y, p);
         }
     }
 }
@@ -253,21 +261,21 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
 // Inverse negacyclic NTT mod kP[pi] of two polynomials at once: row layout
 // (transform order) in, column layout out (natural order), values below 2p;
 // the N^-1 scaling is folded into the key.
-__device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], int pi, uint32_t *xch, int lane)
+__device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], int pi, uint32_t *xch, int lane,
+                                         const uint2 *twl)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
-    const uint32_t *gw = &gW[pi][1][0], *gws = &gWs[pi][1][0];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {            // distance 1 << k: within a lane
         const int dt = 1 << k;
-        const int base = (512 >> k) + (lane << (4 - k));
+        const int base = 32 * (32 - (32 >> k));                  // groups of the earlier stages: 16, 8, 4, 2
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
             const int g = b / dt;
             const int t = g * 2 * dt + (b % dt);
-            const uint32_t w = __ldg(gw + base + g), ws = __ldg(gws + base + g);
-            bf_inv(a[t], a[t + dt], w, ws, p);
-            bf_inv(c[t], c[t + dt], w, ws, p);
+            const uint2 w = twl[base + g * 32 + lane];
+            bf_inv(a[t], a[t + dt], w.x, w.y, p);
+            bf_inv(c[t], c[t + dt], w.x, w.y, p);
         }
     }
     row_to_col(a, xch, lane);
@@ -301,6 +309,11 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
         BrJob j{};
         if (tid < nact) j = jobs[job0 + tid];
         S.job[tid] = j;
+    }
+    {
+        const uint2 *src = &gWL[0][0][0];
+        uint2 *dst = &S.twl[0][0][0];
+        for (int k = tid; k < 4 * kTwLane; k += (WARPS + 1) * 32) dst[k] = src[k];
     }
     if (tid == 0) {
         for (int r = 0; r < kRing; ++r) {
@@ -408,20 +421,21 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
                 const unsigned char *dr = reinterpret_cast<const unsigned char *>(dig + r * (kN / 4));
 #pragma unroll
                 for (int t = 0; t < 32; ++t) x[t] = (uint32_t)dr[lane + 32 * t] - 64u + p;   // digit mod p
-                ntt_fwd(x, pi, xch, lane);
+                ntt_fwd(x, pi, xch, lane, S.twl[pi][0]);
                 const int c = (i * 2 + pi) * kRows + r;               // chunk of the key stream
                 const int slot = c % kRing;
                 mbar_wait(&S.full[slot], (uint32_t)((c / kRing) & 1), err);
-                const uint32_t *b0 = S.ring[slot] + lane;   // [w0 | w0' | w1 | w1'], 1024 words each
+                const uint4 *kv = reinterpret_cast<const uint4 *>(S.ring[slot]) + lane;   // (w0, w0', w1, w1')
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
-                    a0[t] = red2(a0[t] + mul_shoup(x[t], b0[32 * t], b0[kN + 32 * t], p), 2 * p);
-                    a1[t] = red2(a1[t] + mul_shoup(x[t], b0[2 * kN + 32 * t], b0[3 * kN + 32 * t], p), 2 * p);
+                    const uint4 v = kv[32 * t];
+                    a0[t] = red2(a0[t] + mul_shoup(x[t], v.x, v.y, p), 2 * p);
+                    a1[t] = red2(a1[t] + mul_shoup(x[t], v.z, v.w, p), 2 * p);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.empty[slot]);
             }
-            ntt_inv2(a0, a1, pi, xch, lane);
+            ntt_inv2(a0, a1, pi, xch, lane, S.twl[pi][1]);
             if (pi == 0) {
 #pragma unroll
                 for (int t = 0; t < 32; ++t) { a0[t] = red2(a0[t], p); a1[t] = red2(a1[t], p); }
@@ -485,13 +499,14 @@ __global__ void __launch_bounds__(128) bk_ntt_kernel(const uint32_t *__restrict_
     uint32_t x[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) x[t] = src[lane + 32 * t] % p;
-    ntt_fwd(x, pi, xch[warp], lane);
-    uint32_t *dst = out + (id / 2) * kChunkWords + (size_t)j * 2 * kN;
+    ntt_fwd(x, pi, xch[warp], lane, gWL[pi][0]);
+    // chunk layout: [t][lane][w0, w0', w1, w1'] for transform point 32*lane + t
+    uint32_t *dst = out + (id / 2) * kChunkWords + (size_t)j * 2;
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
         const uint32_t v = (uint32_t)(((unsigned long long)(x[t] % p) * cP.scale[pi]) % p);
-        dst[t * 32 + lane] = v;
-        dst[kN + t * 32 + lane] = (uint32_t)(((unsigned long long)v << 32) / p);
+        dst[(t * 32 + lane) * 4] = v;
+        dst[(t * 32 + lane) * 4 + 1] = (uint32_t)(((unsigned long long)v << 32) / p);
     }
 }
 
@@ -542,6 +557,21 @@ int upload_tables()
     if (cudaMemcpyToSymbol(cWs, Ws, sizeof Ws) != cudaSuccess) return -1;
     if (cudaMemcpyToSymbol(gW, W, sizeof W) != cudaSuccess) return -1;
     if (cudaMemcpyToSymbol(gWs, Ws, sizeof Ws) != cudaSuccess) return -1;
+    static uint2 WL[2][2][kTwLane];
+    for (int pi = 0; pi < 2; ++pi)
+        for (int L = 0; L < 32; ++L) {
+            for (int s = 5, base = 0; s < 10; base += 32 << (s - 5), ++s)          // forward, after the transpose
+                for (int g = 0; g < (1 << (s - 5)); ++g) {
+                    const int k = (1 << s) + (L << (s - 5)) + g;
+                    WL[pi][0][base + g * 32 + L] = make_uint2(W[pi][0][k], Ws[pi][0][k]);
+                }
+            for (int k5 = 0, base = 0; k5 < 5; base += 32 * (16 >> k5), ++k5)       // inverse, before the transpose
+                for (int g = 0; g < (16 >> k5); ++g) {
+                    const int k = (512 >> k5) + (L << (4 - k5)) + g;
+                    WL[pi][1][base + g * 32 + L] = make_uint2(W[pi][1][k], Ws[pi][1][k]);
+                }
+        }
+    if (cudaMemcpyToSymbol(gWL, WL, sizeof WL) != cudaSuccess) return -1;
     if (cudaMemcpyToSymbol(cP, &pc, sizeof pc) != cudaSuccess) return -1;
     if (dev >= 0 && dev < 64) g_tables_ready[dev] = true;
     return 0;
@@ -583,8 +613,7 @@ int configure_br_ntt()
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    return (configure_w<5>() | configure_w<6>() | configure_w<7>() | configure_w<8>() | configure_w<9>() |
-            configure_w<10>()) ? -1 : 0;
+    return (configure_w<5>() | configure_w<6>() | configure_w<7>() | configure_w<8>()) ? -1 : 0;
 }
 
 int ntt_warps_min() { return kMinWarps; }
@@ -615,9 +644,7 @@ int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32
     case 5: launch_w<5>(jobs, njobs, bk_ntt, big, err, st); break;
     case 6: launch_w<6>(jobs, njobs, bk_ntt, big, err, st); break;
     case 7: launch_w<7>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 8: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 9: launch_w<9>(jobs, njobs, bk_ntt, big, err, st); break;
-    default: launch_w<10>(jobs, njobs, bk_ntt, big, err, st); break;
+    default: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
     }
     return 1;
 }

@@ -5,7 +5,7 @@
 // t = 8 levels): each extracted mask word a'_i is rounded to 16 bits,
 // abar_i = a'_i + 2^15, split into 8 base-4 digits d_ij (j = 0 most
 // significant), and out = (0, b') - sum_{i,j: d_ij != 0} KSK[i][j][d_ij].
-// It is a gather-sum bound by memory bandwidth: a CTA owns 16 jobs and
+// It is a gather-sum bound by memory bandwidth: a CTA owns 8 or 16 gates and
 // streams each selected 2,528-byte KSK row once for all of them, every
 // thread owning one 16-byte column of the padded 632-word row.
 #include "vp_internal.h"
@@ -13,9 +13,11 @@
 namespace vp {
 namespace {
 
-constexpr int KS_JOBS = 16;
 constexpr int KS_THREADS = 160;  // 158 active 16-byte columns
 
+// KS_JOBS gates per CTA: 16 reuses each gathered row more; 8 gives small
+// layers enough CTAs to fill the GPU.
+template <int KS_JOBS>
 __global__ void __launch_bounds__(KS_THREADS)
 key_switch_kernel(const KsJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ big,
                   const uint4 *__restrict__ ksk)
@@ -113,8 +115,18 @@ int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const u
                       cudaStream_t st)
 {
     if (njobs <= 0) return 0;
-    const int grid = (njobs + KS_JOBS - 1) / KS_JOBS;
-    key_switch_kernel<<<grid, KS_THREADS, 0, st>>>(jobs, njobs, big, reinterpret_cast<const uint4 *>(ksk_dev));
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(ksk_dev);
+    if ((njobs + 15) / 16 < 2 * sms)
+        key_switch_kernel<8><<<(njobs + 7) / 8, KS_THREADS, 0, st>>>(jobs, njobs, big, k4);
+    else
+        key_switch_kernel<16><<<(njobs + 15) / 16, KS_THREADS, 0, st>>>(jobs, njobs, big, k4);
     return 1;
 }
 

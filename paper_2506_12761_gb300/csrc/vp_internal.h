@@ -89,6 +89,7 @@ int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const u
                       cudaStream_t st);
 int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st);
 int launch_pad_ksk(const uint32_t *ksk_abi, uint32_t *ksk_dev, cudaStream_t st);
+int launch_wait_selftest(int *err, cudaStream_t st);   // a bounded wait that is never satisfied
 
 // What an entry point outside api.cu needs from a context.
 struct CtxResources {

@@ -35,6 +35,7 @@ EXPORTS = [
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
+    "velopir_selftest_wait_timeout",
 ]
 NOALLOC_MAX_GATES = 256
 VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "velopir_sync": (i, [vp]),
             "velopir_last_error": (ctypes.c_char_p, [vp]),
             "velopir_launch_count": (u64, [vp]),
+            "velopir_selftest_wait_timeout": (i, [vp]),
             "velopir_client_keygen": (i, [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
             "velopir_client_encrypt_bits": (i, [vp, vp, vp, vp, sz, vp]),
             "velopir_client_decrypt_bits": (i, [vp, vp, sz, vp]),
@@ -239,6 +241,11 @@ def velopir_last_error(ctx) -> str:
 
 def velopir_launch_count(ctx) -> int:
     return int(lib().velopir_launch_count(ctx))
+
+
+def velopir_selftest_wait_timeout(ctx) -> int:
+    """Raw status of the bounded-wait self-test (VELOPIR_ERR_TIMEOUT = -5 is the expected result)."""
+    return int(lib().velopir_selftest_wait_timeout(ctx))
 
 
 def velopir_profile(ctx, enable: bool) -> None:
