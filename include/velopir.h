@@ -216,12 +216,12 @@ int velopir_query_batch(velopir_ctx *ctx, const velopir_query *queries, size_t n
 /* How many times a captured graph was replayed instead of re-captured. */
 uint64_t velopir_graph_replays(velopir_ctx *ctx);
 
-/* Autotuner of the blind-rotation tile shape (bootstraps per CTA, 5..8 for
- * the NTT path).  Times one full wave of each shape on the device and keeps
+/* Autotuner of the blind-rotation tile shape (bootstraps per CTA: 6, 8, 9,
+ * 10 or 12 for the NTT path).  Times one full wave of each shape on the device and keeps
  * the results for this process; afterwards every launch of `count`
  * bootstraps uses the shape with the fewest (waves x measured wave time), so
  * uneven layer sizes waste fewer SMs.  wave_ms_out (nullable, n_out entries)
- * receives the measured wave times in ms, shape 5 first.  A no-op on the
+ * receives the measured wave times in ms, smallest shape first.  A no-op on the
  * dense path.  Errors: ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
 int velopir_autotune(velopir_ctx *ctx, double *wave_ms_out, int n_out);
 

@@ -900,8 +900,8 @@ int velopir_autotune(velopir_ctx *c, double *wave_ms_out, int n_out)
     if (c->path != VP_PATH_NTT) return VELOPIR_OK;   // the dense path has one shape
     int sms = 0;
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const int wmax = ntt_warps_max(), wmin = ntt_warps_min();
-    const int njmax = sms * wmax;
+    const int nshapes = ntt_shape_count();
+    const int njmax = sms * ntt_shape(nshapes - 1);
     if ((rc = ensure(c, c->big, (size_t)njmax * kBigWords * 4))) return rc;
     if ((rc = ensure(c, c->jobs_br, (size_t)njmax * sizeof(BrJob)))) return rc;
     // trivial inputs cost exactly as much as real ones: the kernels do not branch on data
@@ -911,7 +911,8 @@ int velopir_autotune(velopir_ctx *c, double *wave_ms_out, int n_out)
     cudaEvent_t a, b;
     CU(cudaEventCreate(&a));
     CU(cudaEventCreate(&b));
-    for (int w = wmin; w <= wmax; ++w) {
+    for (int si = 0; si < nshapes; ++si) {
+        const int w = ntt_shape(si);
         float best = 0;
         for (int rep = 0; rep < 3; ++rep) {
             CU(cudaEventRecord(a, c->stream));
@@ -924,7 +925,7 @@ int velopir_autotune(velopir_ctx *c, double *wave_ms_out, int n_out)
             if (rep > 0 && (best == 0 || ms < best)) best = ms;   // rep 0 warms up
         }
         ntt_set_wave_ms(w, best);
-        if (wave_ms_out && w - wmin < n_out) wave_ms_out[w - wmin] = best;
+        if (wave_ms_out && si < n_out) wave_ms_out[si] = best;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -4,14 +4,15 @@
 // Per step i the product out_j = sum_r D_r(X) * BK_i[r][j](X) mod (X^N+1) is an
 // integer polynomial whose coefficients are bounded by 6 * N * 64 * 2^32 <
 // 2^50.6 in magnitude (digits |d| <= 64, key words < 2^32).  It is computed
-// modulo p0 = 998244353 and p1 = 1004535809 (both 1 mod 2N, below 2^30) with
+// modulo p0 = 167772161 and p1 = 469762049 (both 1 mod 2N, below 2^29) with
 // negacyclic NTTs, recombined by the Chinese remainder theorem into the exact
-// signed integer (p0 * p1 > 2^59.7), and reduced mod 2^32: bit-identical to
-// the dense contraction.
+// signed integer (p0 * p1 > 2^56), and reduced mod 2^32: bit-identical to the
+// dense contraction.
 //
 // Transform: Cooley-Tukey forward / Gentleman-Sande inverse with the powers of
 // a primitive 2N-th root psi in bit-reversed order (the merged negacyclic
-// form), Shoup multiplications with lazy reduction (values kept below 4p).
+// form), Shoup multiplications with lazy reduction: forward values stay below
+// 8p < 2^32 and are reduced only every other stage.
 // The pointwise products are Shoup multiplications by the transformed key,
 // stored with N^-1 folded in and with each value's Shoup companion.
 //
@@ -19,10 +20,10 @@
 // warp's registers, 32 points per lane; the five stages whose pairs lie in
 // one lane run in registers, a padded 32x33 shared-memory transpose moves to
 // the other lane grouping, and five more stages run in registers.  No block
-// barrier is involved: each warp synchronises only itself.  A producer warp
-// streams each step's transformed key, one prime (48 KB) at a time, into a
-// double buffer with bulk asynchronous copies; full/empty mbarriers hand the
-// halves between producer and compute warps.
+// barrier is involved: each warp synchronises only itself.  Warp 0 also
+// streams the transformed key in 16 KB chunks (one step, prime and row) into a
+// ring with bulk asynchronous copies; full/empty mbarriers hand the chunks
+// between warp 0 (which issues the copies) and all compute warps.
 #include <cstdio>
 #include <vector>
 
@@ -31,11 +32,12 @@
 namespace vp {
 namespace {
 
-constexpr int kMinWarps = 5;                   // compute warps = bootstraps per CTA (5..8, chosen per launch)
-constexpr int kMaxWarps = 8;
+constexpr int kShapes[5] = {6, 8, 9, 10, 12}; // compute warps = bootstraps per CTA, chosen per launch
+constexpr int kMaxWarps = 12;
 constexpr int kTwLane = 31 * 32;               // lane-dependent twiddles of one transform: 31 groups x 32 lanes
-constexpr uint32_t kTmemCols = 256;            // per CTA: up to 2 warps share a 32-lane quarter, 64 columns each
-constexpr uint32_t kP[2] = {998244353u, 1004535809u};
+constexpr uint32_t kTmemCols = 512;            // per CTA: up to 3 warps share a 32-lane quarter, 112 columns each
+constexpr uint32_t kTmemWarpCols = 112;        // per warp: 64 for the product mod p0, 48 for the packed digits
+constexpr uint32_t kP[2] = {167772161u, 469762049u};   // p0 < p1: the CRT below relies on it
 constexpr int kXch = 32 * 33;                  // padded transpose tile
 constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
 constexpr int kChunks = kn * 2 * kRows;        // consumed in this order: step, prime, row
@@ -66,7 +68,6 @@ template <int WARPS> struct __align__(128) Smem {
     uint32_t ring[kRing][kChunkWords];    // 2 x 16 KB: stream of the transformed key
     uint2 twl[2][2][kTwLane];             // 31 KB: lane-dependent twiddles [prime][direction]
     uint32_t acc[WARPS][2 * kN];          // 8 KB per warp: ACC of its bootstrap
-    uint32_t dig[WARPS][kRows * kN / 4];  // 6 KB per warp: digit polynomials (digit + 64), one byte each
     uint32_t xch[WARPS][kXch];            // 4.1 KB per warp: transpose tile
     uint16_t abar[WARPS][kSlotWords];     // modulus-switched input
     BrJob job[WARPS];
@@ -118,8 +119,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     }
 }
 
-// Bounded wait that ignores the error word: used by the producer to let its
-// own copies land before the CTA exits.
+// Bounded wait that ignores the error word: lets copies still in flight land
+// before the CTA exits.
 __device__ __forceinline__ void mbar_drain(unsigned long long *bar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
@@ -174,6 +175,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // x * w mod p in [0, 2p) for any x < 2^32 (Shoup, ws = floor(w 2^32 / p)).
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p)
 {
@@ -183,12 +203,14 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 
 __device__ __forceinline__ uint32_t red2(uint32_t x, uint32_t m) { return min(x, x - m); }  // [0,2m) -> [0,m)
 
-// Cooley-Tukey butterfly, inputs and outputs below 4p (inputs below 2p when
-// kReduced, which skips the reduction of X).
-template <bool kReduced = false>
+// Cooley-Tukey butterfly.  kReduce: inputs below 8p, X first brought below
+// 4p (one conditional subtraction of 4p), outputs below 6p.  Otherwise:
+// inputs below 6p, outputs below 8p.  With p < 2^29 every value fits in 32
+// bits, so stages alternate and half of them skip the reduction.
+template <bool kReduce>
 __device__ __forceinline__ void bf_fwd(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
 {
-    const uint32_t x = kReduced ? X : red2(X, 2 * p);
+    const uint32_t x = kReduce ? red2(X, 4 * p) : X;
     const uint32_t t = mul_shoup(Y, w, ws, p);
     X = x + t;
     Y = x - t + 2 * p;
@@ -224,8 +246,8 @@ __device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int l
     __syncwarp();
 }
 
-// Forward negacyclic NTT mod kP[pi] of one polynomial: column layout in,
-// row layout out (transform order), values below 4p.  Every loop has a
+// Forward negacyclic NTT mod kP[pi] of one polynomial: column layout in
+// (values below 2p), row layout out (transform order), values below 6p.  Every loop has a
 // compile-time trip count and every array index is a compile-time constant,
 // so the 32 points stay in registers.
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane, const uint2 *twl)
@@ -239,8 +261,8 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
         for (int b = 0; b < 16; ++b) {
             const int t = (b / dt) * 2 * dt + (b % dt);
             const int k = (1 << s) + (t >> (5 - s));
-            if (s == 0) bf_fwd<true>(x[t], x[t + dt], cw[k], cws[k], p);   // inputs are below 2p
-            else bf_fwd(x[t], x[t + dt], cw[k], cws[k], p);
+            if (s & 1) bf_fwd<true>(x[t], x[t + dt], cw[k], cws[k], p);   // stage 0 inputs are below 2p
+            else bf_fwd<false>(x[t], x[t + dt], cw[k], cws[k], p);
         }
     }
     col_to_row(x, xch, lane);
@@ -253,7 +275,8 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
             const int g = b / dt;                                  // group of this lane's points
             const int t = g * 2 * dt + (b % dt);
             const uint2 w = twl[base + g * 32 + lane];
-            bf_fwd(x[t], x[t + dt], w.x, w.y, p);
+            if (s & 1) bf_fwd<true>(x[t], x[t + dt], w.x, w.y, p);
+            else bf_fwd<false>(x[t], x[t + dt], w.x, w.y, p);
         }
     }
 }
@@ -295,7 +318,7 @@ __device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], i
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__((WARPS + 1) * 32, 1)
+__global__ void __launch_bounds__(WARPS * 32, 1)
 br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ bkhat,
               uint32_t *__restrict__ big, int *err)
 {
@@ -313,7 +336,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
     {
         const uint2 *src = &gWL[0][0][0];
         uint2 *dst = &S.twl[0][0][0];
-        for (int k = tid; k < 4 * kTwLane; k += (WARPS + 1) * 32) dst[k] = src[k];
+        for (int k = tid; k < 4 * kTwLane; k += WARPS * 32) dst[k] = src[k];
     }
     if (tid == 0) {
         for (int r = 0; r < kRing; ++r) {
@@ -332,31 +355,19 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (warp == WARPS) {
-        // Producer: stream the transformed key chunk by chunk (step, prime,
-        // row) through the ring; a slot is refilled once every compute warp
-        // has released its previous chunk.
-        if (lane == 0) {
-            int issued = 0;
-            for (int c = 0; c < kChunks; ++c) {
-                const int slot = c % kRing;
-                if (c >= kRing && !mbar_wait(&S.empty[slot], (uint32_t)((c / kRing - 1) & 1), err)) break;
-                load_chunk(S.ring[slot], bkhat + (size_t)c * kChunkWords, &S.full[slot]);
-                issued = c + 1;
-            }
-            // every issued copy must land before this CTA's shared memory is released
-            for (int c = (issued > kRing ? issued - kRing : 0); c < issued; ++c)
-                mbar_drain(&S.full[c % kRing], (uint32_t)((c / kRing) & 1));
-        }
-        return;
-    }
+    // Warp 0 keeps the key stream kRing chunks ahead: it issues the first
+    // chunks now and chunk c + kRing once every warp has released chunk c.
+    if (warp == 0 && lane == 0)
+        for (int c = 0; c < kRing && c < kChunks; ++c)
+            load_chunk(S.ring[c], bkhat + (size_t)c * kChunkWords, &S.full[c]);
     if (warp >= nact) return;
 
     const BrJob J = S.job[warp];
     uint32_t *acc = S.acc[warp];
-    uint32_t *dig = S.dig[warp];
-    // this warp's 64 columns in its lane quarter: [0, 32) component a, [32, 64) component b
-    const uint32_t tres = S.tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * (warp >> 2));
+    // this warp's columns in its lane quarter: [0, 32) and [32, 64) the product mod p0
+    // (components a, b); [64, 112) the digit polynomials, 8 packed words per row
+    const uint32_t tres = S.tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + kTmemWarpCols * (uint32_t)(warp >> 2);
+    const uint32_t tdig = tres + 64;
     uint32_t *xch = S.xch[warp];
     uint16_t *abar = S.abar[warp];
 
@@ -388,10 +399,14 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
     for (int i = 0; i < kn; ++i) {
         const uint32_t ab = abar[i];
         // Rotate, subtract, decompose into 6 digit polynomials (row r = 2(p-1)+q),
-        // stored as digit + 64 in one byte; lanes take consecutive coefficients.
+        // digit + 64 packed four per word; lane L owns coefficients L + 32m,
+        // which are exactly the points it feeds into the forward transforms,
+        // so the digits stay in its Tensor Memory lane.
         {
-            unsigned char *d8 = reinterpret_cast<unsigned char *>(dig);
-#pragma unroll 2
+            uint32_t packed[kRows * 8];
+#pragma unroll
+            for (int w = 0; w < kRows * 8; ++w) packed[w] = 0u;
+#pragma unroll
             for (int m = 0; m < 32; ++m) {
                 const int k = lane + 32 * m;
                 const uint32_t src = ((uint32_t)k - ab) & (kTwoN - 1);
@@ -401,11 +416,16 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
                     uint32_t v = a[src & (kN - 1)];
                     if (src >= (uint32_t)kN) v = 0u - v;
                     const uint32_t y = v - a[k] + kOff;
-                    d8[(0 * 2 + q) * kN + k] = (unsigned char)((y >> 25) & 127u);
-                    d8[(1 * 2 + q) * kN + k] = (unsigned char)((y >> 18) & 127u);
-                    d8[(2 * 2 + q) * kN + k] = (unsigned char)((y >> 11) & 127u);
+                    const int sh = 8 * (m & 3), w = m >> 2;
+                    packed[(0 * 2 + q) * 8 + w] |= ((y >> 25) & 127u) << sh;
+                    packed[(1 * 2 + q) * 8 + w] |= ((y >> 18) & 127u) << sh;
+                    packed[(2 * 2 + q) * 8 + w] |= ((y >> 11) & 127u) << sh;
                 }
             }
+            tmem_st16(tdig, packed);
+            tmem_st16(tdig + 16, packed + 16);
+            tmem_st16(tdig + 32, packed + 32);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         __syncwarp();
 
@@ -417,10 +437,10 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
             for (int t = 0; t < 32; ++t) { a0[t] = 0u; a1[t] = 0u; }
 #pragma unroll 1
             for (int r = 0; r < kRows; ++r) {
-                uint32_t x[32];
-                const unsigned char *dr = reinterpret_cast<const unsigned char *>(dig + r * (kN / 4));
+                uint32_t x[32], dw[8];
+                tmem_ld8(tdig + 8 * r, dw);
 #pragma unroll
-                for (int t = 0; t < 32; ++t) x[t] = (uint32_t)dr[lane + 32 * t] - 64u + p;   // digit mod p
+                for (int t = 0; t < 32; ++t) x[t] = ((dw[t >> 2] >> (8 * (t & 3))) & 0xFFu) - 64u + p;   // digit mod p
                 ntt_fwd(x, pi, xch, lane, S.twl[pi][0]);
                 const int c = (i * 2 + pi) * kRows + r;               // chunk of the key stream
                 const int slot = c % kRing;
@@ -433,7 +453,13 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
                     a1[t] = red2(a1[t] + mul_shoup(x[t], v.z, v.w, p), 2 * p);
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&S.empty[slot]);
+                if (lane == 0) {
+                    mbar_arrive(&S.empty[slot]);
+                    if (warp == 0 && c + kRing < kChunks &&
+                        mbar_wait(&S.empty[slot], (uint32_t)((c / kRing) & 1), err))
+                        load_chunk(S.ring[slot], bkhat + (size_t)(c + kRing) * kChunkWords, &S.full[slot]);
+                }
+                __syncwarp();
             }
             ntt_inv2(a0, a1, pi, xch, lane, S.twl[pi][1]);
             if (pi == 0) {
@@ -468,6 +494,11 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restr
     uint32_t *row = big + (size_t)J.big * kBigWords;
     for (int k = lane; k < kN; k += 32) row[k == 0 ? 0 : kN - k] = k == 0 ? acc[0] : 0u - acc[k];
     if (lane == 0) row[kN] = acc[kN];
+
+    // Copies still in flight after a timed-out wait must land before the
+    // shared memory is released.
+    if (warp == 0 && lane == 0 && *reinterpret_cast<volatile int *>(err) != kDevOk)
+        for (int r = 0; r < kRing; ++r) mbar_drain(&S.full[r], 0u), mbar_drain(&S.full[r], 1u);
 
     // All active compute warps are done with Tensor Memory: warp 0 frees it.
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -586,13 +617,14 @@ template <int W> int configure_w()
 template <int W> void launch_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err,
                                cudaStream_t st)
 {
-    br_ntt_kernel<W><<<(njobs + W - 1) / W, (W + 1) * 32, sizeof(Smem<W>), st>>>(jobs, njobs, bk_ntt, big, err);
+    br_ntt_kernel<W><<<(njobs + W - 1) / W, W * 32, sizeof(Smem<W>), st>>>(jobs, njobs, bk_ntt, big, err);
 }
 
 // Tuned per-wave time of each variant (ms for one full wave of 152 CTAs);
 // zero until velopir's autotuner has measured it.
 float g_wave_ms[kMaxWarps + 1] = {0};
 static_assert(sizeof(Smem<kMaxWarps>) <= 232448, "shared memory per CTA");
+static_assert(3 * kTmemWarpCols <= kTmemCols, "Tensor Memory per CTA");
 int g_sms = 0;
 
 }  // namespace
@@ -613,25 +645,26 @@ int configure_br_ntt()
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    return (configure_w<5>() | configure_w<6>() | configure_w<7>() | configure_w<8>()) ? -1 : 0;
+    return (configure_w<6>() | configure_w<8>() | configure_w<9>() | configure_w<10>() | configure_w<12>()) ? -1 : 0;
 }
 
-int ntt_warps_min() { return kMinWarps; }
-int ntt_warps_max() { return kMaxWarps; }
-void ntt_set_wave_ms(int warps, float ms) { if (warps >= kMinWarps && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
+int ntt_shape_count() { return 5; }
+int ntt_shape(int i) { return kShapes[i]; }
+void ntt_set_wave_ms(int warps, float ms) { if (warps >= 1 && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
 
-// Bootstraps per CTA for a launch of njobs: the variant with the smallest
+// Bootstraps per CTA for a launch of njobs: the shape with the smallest
 // (waves x tuned wave time); without tuning, the largest CTA.
 int ntt_pick_warps(int njobs)
 {
     int best = kMaxWarps;
     double best_t = 0;
     const int sms = g_sms > 0 ? g_sms : 152;
-    for (int w = kMinWarps; w <= kMaxWarps; ++w) {
+    for (int i = 0; i < 5; ++i) {
+        const int w = kShapes[i];
         if (g_wave_ms[w] <= 0) return kMaxWarps;
         const int ctas = (njobs + w - 1) / w;
         const double t = (double)((ctas + sms - 1) / sms) * g_wave_ms[w];
-        if (w == kMinWarps || t < best_t) { best = w; best_t = t; }
+        if (i == 0 || t < best_t) { best = w; best_t = t; }
     }
     return best;
 }
@@ -641,10 +674,11 @@ int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32
 {
     if (njobs <= 0) return 0;
     switch (warps) {
-    case 5: launch_w<5>(jobs, njobs, bk_ntt, big, err, st); break;
     case 6: launch_w<6>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 7: launch_w<7>(jobs, njobs, bk_ntt, big, err, st); break;
-    default: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 8: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 9: launch_w<9>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 10: launch_w<10>(jobs, njobs, bk_ntt, big, err, st); break;
+    default: launch_w<12>(jobs, njobs, bk_ntt, big, err, st); break;
     }
     return 1;
 }

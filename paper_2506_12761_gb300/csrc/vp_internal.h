@@ -79,8 +79,8 @@ int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t
 int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st);
 int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st,
                     int warps);                 // a fixed variant: `warps` bootstraps per CTA
-int ntt_warps_min();
-int ntt_warps_max();
+int ntt_shape_count();                         // tile shapes of the NTT kernel (bootstraps per CTA)
+int ntt_shape(int i);                          // the i-th shape, ascending
 int ntt_pick_warps(int njobs);                 // the tuned choice for a launch of njobs
 void ntt_set_wave_ms(int warps, float ms);     // record a measured full-wave time
 size_t bk_ntt_words();

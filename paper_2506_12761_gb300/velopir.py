@@ -38,6 +38,7 @@ EXPORTS = [
     "velopir_selftest_wait_timeout",
 ]
 NOALLOC_MAX_GATES = 256
+NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
 VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
 
 
@@ -184,7 +185,7 @@ def velopir_graph_replays(ctx) -> int:
 
 
 def velopir_autotune(ctx) -> list[float]:
-    """Measured full-wave times (ms) of the blind-rotation shapes, 5 bootstraps per CTA first."""
+    """Measured full-wave times (ms) of the blind-rotation tile shapes (6, 8, 9, 10, 12 bootstraps per CTA)."""
     out = (ctypes.c_double * 8)()
     _check(ctx, lib().velopir_autotune(ctx, out, 8))
     return [x for x in out if x > 0]
