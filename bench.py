@@ -324,8 +324,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
                            "path": args.path, "parallelism": f"replicas x{world}",
-                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves)),
-                                           "chosen": {n: vp.velopir_tuned_shape(ctx.h, n) for n in (1024, 2048, 4096)}},
+                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves))},
                            "l2": "flushed between timed steps (256 MiB write, untimed)"},
                 "query_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
                 "plain": {"value": plain_rate, "unit": UNIT, "note": "one bootstrap per kernel launch, same kernels"},

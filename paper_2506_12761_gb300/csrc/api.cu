@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/velopir.h"
 #include "sched.h"
 #include "vp_internal.h"
@@ -287,7 +289,10 @@ int issue_graph(velopir_ctx *c, const Flat &F)
 
 int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
 {
+    // one NVTX range per launch (kind and size) for timeline tools
+    static const char *names[3] = {"velopir:blind_rotate", "velopir:key_switch", "velopir:free_gates"};
     for (const Launch &l : F.launches) {
+        nvtxRangePushA(names[l.kind]);
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (c->prof) {
             for (cudaEvent_t *e : {&ea, &eb}) {
@@ -300,6 +305,7 @@ int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBu
         else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), c->stream);
         else c->launches += launch_free(as<FreeJob>(dfr) + l.off, l.n, c->stream);
         CU(cudaGetLastError());
+        nvtxRangePop();
         if (c->prof) {
             CU(cudaEventRecord(eb, c->stream));
             c->recs.push_back({l.kind, (uint64_t)l.n, ea, eb});

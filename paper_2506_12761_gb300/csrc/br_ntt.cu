@@ -24,7 +24,9 @@
 // streams the transformed key in 16 KB chunks (one step, prime and row) into a
 // ring with bulk asynchronous copies; full/empty mbarriers hand the chunks
 // between warp 0 (which issues the copies) and all compute warps.
+#include <algorithm>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "vp_internal.h"
@@ -317,16 +319,17 @@ __device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], i
     }
 }
 
+// CTA c takes jobs [c * per, c * per + per) (per <= WARPS); its other warps idle.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1)
-br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ bkhat,
+br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t *__restrict__ bkhat,
               uint32_t *__restrict__ big, int *err)
 {
     extern __shared__ unsigned char smem_raw[];
     Smem<WARPS> &S = *reinterpret_cast<Smem<WARPS> *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int job0 = blockIdx.x * WARPS;
-    const int nact = min(WARPS, njobs - job0);
+    const int job0 = blockIdx.x * per;
+    const int nact = min(per, njobs - job0);
 
     if (tid < WARPS) {
         BrJob j{};
@@ -614,10 +617,10 @@ template <int W> int configure_w()
                                 (int)sizeof(Smem<W>)) == cudaSuccess ? 0 : -1;
 }
 
-template <int W> void launch_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err,
-                               cudaStream_t st)
+template <int W> void launch_w(const BrJob *jobs, int njobs, int per, const uint32_t *bk_ntt, uint32_t *big,
+                               int *err, cudaStream_t st)
 {
-    br_ntt_kernel<W><<<(njobs + W - 1) / W, W * 32, sizeof(Smem<W>), st>>>(jobs, njobs, bk_ntt, big, err);
+    br_ntt_kernel<W><<<(njobs + per - 1) / per, W * 32, sizeof(Smem<W>), st>>>(jobs, njobs, per, bk_ntt, big, err);
 }
 
 // Tuned per-wave time of each variant (ms for one full wave of 152 CTAs);
@@ -669,23 +672,85 @@ int ntt_pick_warps(int njobs)
     return best;
 }
 
+namespace {
+
+// The tuned shape with the shortest wave time among those holding b
+// bootstraps per CTA (a partly filled CTA runs about as long as a full one).
+int shape_for(int b)
+{
+    int best = -1;
+    for (int i = 0; i < 5; ++i) {
+        const int w = kShapes[i];
+        if (w >= b && (best < 0 || g_wave_ms[w] < g_wave_ms[best])) best = w;
+    }
+    return best < 0 ? kMaxWarps : best;
+}
+
+// Wave plan of a launch: the per-SM load L = ceil(njobs / SMs) is split into
+// waves of b_i bootstraps per CTA (sum b_i = L), minimising the sum of the
+// tuned wave times of the shapes that hold them.  A wave of b per CTA costs
+// about the wave time of its shape whether or not the shape is full, because
+// each warp runs at a latency-bound speed; the plan therefore prefers full
+// 12-wide waves and covers the remainder with waves that keep at most two
+// warps per SM sub-partition.
+struct Wave { int shape, per; };
+
+const std::vector<Wave> &plan_waves(int njobs)
+{
+    static std::vector<std::pair<int, std::vector<Wave>>> cache;
+    for (auto &e : cache)
+        if (e.first == njobs) return e.second;
+    const int sms = g_sms > 0 ? g_sms : 152;
+    const int L = (njobs + sms - 1) / sms;
+    std::vector<double> cost(L + 1, 0.0);
+    std::vector<int> choice(L + 1, 0);
+    for (int l = 1; l <= L; ++l) {
+        cost[l] = -1;
+        for (int b = 1; b <= kMaxWarps && b <= l; ++b) {
+            const double c = cost[l - b] + g_wave_ms[shape_for(b)];
+            if (cost[l] < 0 || c < cost[l] - 1e-9) { cost[l] = c; choice[l] = b; }
+        }
+    }
+    std::vector<Wave> plan;
+    for (int l = L; l > 0; l -= choice[l]) plan.push_back({shape_for(choice[l]), choice[l]});
+    std::sort(plan.begin(), plan.end(), [](const Wave &a, const Wave &b) { return a.per > b.per; });
+    if (cache.size() > 256) cache.clear();
+    cache.emplace_back(njobs, plan);
+    return cache.back().second;
+}
+
+}  // namespace
+
 int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st,
-                    int warps)
+                    int warps, int per)
 {
     if (njobs <= 0) return 0;
+    if (per <= 0 || per > warps) per = warps;
     switch (warps) {
-    case 6: launch_w<6>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 8: launch_w<8>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 9: launch_w<9>(jobs, njobs, bk_ntt, big, err, st); break;
-    case 10: launch_w<10>(jobs, njobs, bk_ntt, big, err, st); break;
-    default: launch_w<12>(jobs, njobs, bk_ntt, big, err, st); break;
+    case 6: launch_w<6>(jobs, njobs, per, bk_ntt, big, err, st); break;
+    case 8: launch_w<8>(jobs, njobs, per, bk_ntt, big, err, st); break;
+    case 9: launch_w<9>(jobs, njobs, per, bk_ntt, big, err, st); break;
+    case 10: launch_w<10>(jobs, njobs, per, bk_ntt, big, err, st); break;
+    default: launch_w<12>(jobs, njobs, per, bk_ntt, big, err, st); break;
     }
     return 1;
 }
 
 int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st)
 {
-    return launch_br_ntt_w(jobs, njobs, bk_ntt, big, err, st, ntt_pick_warps(njobs));
+    if (njobs <= 0) return 0;
+    for (int i = 0; i < 5; ++i)
+        if (g_wave_ms[kShapes[i]] <= 0)   // not tuned: one launch of the widest shape
+            return launch_br_ntt_w(jobs, njobs, bk_ntt, big, err, st, kMaxWarps, kMaxWarps);
+    const int sms = g_sms > 0 ? g_sms : 152;
+    int launches = 0, off = 0;
+    for (const Wave &w : plan_waves(njobs)) {
+        if (off >= njobs) break;
+        const int n = std::min(njobs - off, sms * w.per);
+        launches += launch_br_ntt_w(jobs + off, n, bk_ntt, big, err, st, w.shape, w.per);
+        off += n;
+    }
+    return launches;
 }
 
 }  // namespace vp

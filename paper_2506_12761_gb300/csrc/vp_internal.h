@@ -78,7 +78,7 @@ int launch_br_ntt(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t
                   cudaStream_t st);
 int prepare_bk_ntt(const uint32_t *bk, uint32_t *bk_ntt, cudaStream_t st);
 int launch_br_ntt_w(const BrJob *jobs, int njobs, const uint32_t *bk_ntt, uint32_t *big, int *err, cudaStream_t st,
-                    int warps);                 // a fixed variant: `warps` bootstraps per CTA
+                    int warps, int per = 0);    // a fixed shape of `warps` warps, `per` (<= warps) bootstraps per CTA
 int ntt_shape_count();                         // tile shapes of the NTT kernel (bootstraps per CTA)
 int ntt_shape(int i);                          // the i-th shape, ascending
 int ntt_pick_warps(int njobs);                 // the tuned choice for a launch of njobs

@@ -128,3 +128,21 @@ def test_submit_errors():
         vp.velopir_submit(ctx.h, bad)
     with pytest.raises(vp.VelopirError):
         vp.velopir_poll(ctx.h, 10 ** 9)
+
+
+def test_progress_reports_every_ticket_once():
+    """velopir_progress steps the loop and reports each finished ticket once;
+    results equal the queries run alone."""
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 6)
+    alone = [run_alone(ctx, q) for q in qs]
+    tickets = {vp.velopir_submit(ctx.h, as_record(q)): i for i, q in enumerate(qs)}
+    seen = []
+    for _ in range(500):
+        seen += vp.velopir_progress(ctx.h)
+        if len(seen) == len(qs):
+            break
+    assert sorted(seen) == sorted(tickets)
+    assert vp.velopir_progress(ctx.h) == []
+    for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], a)
