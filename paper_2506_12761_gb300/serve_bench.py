@@ -88,7 +88,7 @@ def check(s, queries):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--per-point", type=int, default=10)
+    ap.add_argument("--per-point", type=int, default=8)
     ap.add_argument("--capacity-queries", type=int, default=8)
     ap.add_argument("--loads", default="0.5,1.0,1.5")
     ap.add_argument("--budget-gb", type=float, default=96.0)
