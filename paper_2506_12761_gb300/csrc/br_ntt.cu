@@ -40,19 +40,18 @@ constexpr int kTwLane = 31 * 32;               // lane-dependent twiddles of one
 constexpr uint32_t kTmemCols = 512;            // per CTA: up to 3 warps share a 32-lane quarter, 112 columns each
 constexpr uint32_t kTmemWarpCols = 112;        // per warp: 64 for the product mod p0, 48 for the packed digits
 constexpr uint32_t kP[2] = {167772161u, 469762049u};   // p0 < p1: the CRT below relies on it
-constexpr int kXch = 32 * 33;                  // padded transpose tile
+constexpr uint32_t kPmod32 = (uint32_t)(167772161ull * 469762049ull);   // p0 p1 mod 2^32
+constexpr int kXch = 32 * 32;                  // transpose tile (16-byte chunks XOR-swizzled by row)
 constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
 constexpr int kChunks = kn * 2 * kRows;        // consumed in this order: step, prime, row
 constexpr size_t kBkNttWords = (size_t)kChunks * kChunkWords;
 constexpr int kRing = 2;                       // ring slots of the key stream
 
-// Twiddles psi^(+-brv(k)) and their Shoup companions floor(w * 2^32 / p):
-// [prime][0 = forward, 1 = inverse][k].  Uniformly indexed stages read the
-// constant bank; lane-dependent stages read the global copy.
-__constant__ uint32_t cW[2][2][kN];
-__constant__ uint32_t cWs[2][2][kN];
-__device__ uint32_t gW[2][2][kN];
-__device__ uint32_t gWs[2][2][kN];
+// Twiddles psi^(+-brv(k)) with their Shoup companions floor(w * 2^32 / p) as
+// (w, w') pairs: [prime][0 = forward, 1 = inverse][k].  Uniformly indexed
+// stages read the constant bank (one 8-byte load per pair); lane-dependent
+// stages read the shared-memory copy of gWL below.
+__constant__ uint2 cWp[2][2][kN];
 // The lane-dependent twiddles of the in-lane stages after (forward) or before
 // (inverse) the transpose, as (w, w') pairs in [stage][group][lane] order so
 // that a warp reads them from shared memory without bank conflicts.
@@ -102,18 +101,27 @@ __device__ __forceinline__ uint64_t global_ns()
 // Wait on the mbarrier phase `parity` for at most kWaitNs; on timeout record
 // it in the error word and return false.  Once any wait has given up, later
 // waits return at once, so a failed launch ends quickly instead of spinning.
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// A phase that has already completed returns at once, without touching the
+// error word or the timer (the common case: the chunk landed during the
+// transform).  Otherwise the wait is bounded as above.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *err)
 {
+    if (mbar_try(bar, parity)) return true;
     if (*reinterpret_cast<volatile int *>(err) != kDevOk) return false;
     const uint64_t t0 = global_ns();
     for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(bar, parity)) return true;
         if (global_ns() - t0 > kWaitNs) {
             atomicExch(err, kDevTimeout);
             return false;
@@ -126,14 +134,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
 __device__ __forceinline__ void mbar_drain(unsigned long long *bar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok || global_ns() - t0 > kWaitNs) return;
+    while (!mbar_try(bar, parity) && global_ns() - t0 <= kWaitNs) {
     }
 }
 
@@ -196,6 +197,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Issue a load of 8 columns without waiting: the registers are valid only
+// after tmem_wait_ld(), and nothing may read them before.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // x * w mod p in [0, 2p) for any x < 2^32 (Shoup, ws = floor(w 2^32 / p)).
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p)
 {
@@ -204,6 +217,16 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 }
 
 __device__ __forceinline__ uint32_t red2(uint32_t x, uint32_t m) { return min(x, x - m); }  // [0,2m) -> [0,m)
+
+// x mod p into [0, 2p) for any x < 2^32: Shoup's reduction with w = 1, pinv = floor(2^32 / p).
+__device__ __forceinline__ uint32_t red_shoup(uint32_t x, uint32_t pinv, uint32_t p) { return x - __umulhi(x, pinv) * p; }
+
+// Bits [s, s + 7) of y placed at bits [b, b + 7), everything else zero (s and b
+// are constants after unrolling: one shift and one masked OR).
+__device__ __forceinline__ uint32_t field7(uint32_t y, int s, int b)
+{
+    return (s >= b ? (y >> (s - b)) : (y << (b - s))) & (127u << b);
+}
 
 // Cooley-Tukey butterfly.  kReduce: inputs below 8p, X first brought below
 // 4p (one conditional subtraction of 4p), outputs below 6p.  Otherwise:
@@ -226,25 +249,20 @@ __device__ __forceinline__ void bf_inv(uint32_t &X, uint32_t &Y, uint32_t w, uin
     Y = mul_shoup(x - y + 2 * p, w, ws, p);
 }
 
-// Lane L holds point L + 32t -> lane L holds point 32L + t.
-__device__ __forceinline__ void col_to_row(uint32_t (&x)[32], uint32_t *m, int lane)
+// 32x32 transpose of a warp's registers through shared memory: lane L's x[t]
+// becomes lane t's x[L].  It maps the column layout (lane L holds points
+// L + 32t) to the row layout (lane L holds points 32L + t) and back.  Each
+// lane stores its 32 values as one row with 16-byte stores whose chunk
+// order is XOR-swizzled by the row, so both the stores (8 lanes per 128-byte
+// wavefront) and the column reads hit 32 distinct banks.
+__device__ __forceinline__ void transpose32(uint32_t (&x)[32], uint32_t *m, int lane)
 {
+    uint4 *row = reinterpret_cast<uint4 *>(m + 32 * lane);
 #pragma unroll
-    for (int t = 0; t < 32; ++t) m[t * 33 + lane] = x[t];
+    for (int j = 0; j < 8; ++j) row[j ^ (lane & 7)] = make_uint4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
     __syncwarp();
 #pragma unroll
-    for (int t = 0; t < 32; ++t) x[t] = m[lane * 33 + t];
-    __syncwarp();
-}
-
-// Lane L holds point 32L + t -> lane L holds point L + 32t.
-__device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int lane)
-{
-#pragma unroll
-    for (int t = 0; t < 32; ++t) m[lane * 33 + t] = x[t];
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 32; ++t) x[t] = m[t * 33 + lane];
+    for (int t = 0; t < 32; ++t) x[t] = m[32 * t + 4 * ((lane >> 2) ^ (t & 7)) + (lane & 3)];
     __syncwarp();
 }
 
@@ -255,7 +273,7 @@ __device__ __forceinline__ void row_to_col(uint32_t (&x)[32], uint32_t *m, int l
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane, const uint2 *twl)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
-    const uint32_t *cw = &cW[pi][0][0], *cws = &cWs[pi][0][0];
+    const uint2 *cw = &cWp[pi][0][0];
 #pragma unroll
     for (int s = 0; s < 5; ++s) {            // distance 512 >> s: within a lane
         const int dt = 16 >> s;
@@ -263,11 +281,12 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
         for (int b = 0; b < 16; ++b) {
             const int t = (b / dt) * 2 * dt + (b % dt);
             const int k = (1 << s) + (t >> (5 - s));
-            if (s & 1) bf_fwd<true>(x[t], x[t + dt], cw[k], cws[k], p);   // stage 0 inputs are below 2p
-            else bf_fwd<false>(x[t], x[t + dt], cw[k], cws[k], p);
+            const uint2 w = cw[k];
+            if (s & 1) bf_fwd<true>(x[t], x[t + dt], w.x, w.y, p);   // stage 0 inputs are below 2p
+            else bf_fwd<false>(x[t], x[t + dt], w.x, w.y, p);
         }
     }
-    col_to_row(x, xch, lane);
+    transpose32(x, xch, lane);
 #pragma unroll
     for (int s = 5; s < 10; ++s) {           // distance 512 >> s < 32: within a lane after the transpose
         const int dt = 1 << (9 - s);
@@ -303,9 +322,9 @@ __device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], i
             bf_inv(c[t], c[t + dt], w.x, w.y, p);
         }
     }
-    row_to_col(a, xch, lane);
-    row_to_col(c, xch, lane);
-    const uint32_t *cw = &cW[pi][1][0], *cws = &cWs[pi][1][0];
+    transpose32(a, xch, lane);
+    transpose32(c, xch, lane);
+    const uint2 *cw = &cWp[pi][1][0];
 #pragma unroll
     for (int k = 5; k < 10; ++k) {           // distance 32 << (k-5): within a lane
         const int dt = 1 << (k - 5);
@@ -313,8 +332,9 @@ __device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], i
         for (int b = 0; b < 16; ++b) {
             const int t = (b / dt) * 2 * dt + (b % dt);
             const int idx = (512 >> k) + (t >> (k - 4));
-            bf_inv(a[t], a[t + dt], cw[idx], cws[idx], p);
-            bf_inv(c[t], c[t + dt], cw[idx], cws[idx], p);
+            const uint2 w = cw[idx];
+            bf_inv(a[t], a[t + dt], w.x, w.y, p);
+            bf_inv(c[t], c[t + dt], w.x, w.y, p);
         }
     }
 }
@@ -395,8 +415,6 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 
     constexpr uint32_t kOff = (1u << 31) + (1u << 24) + (1u << 17) + (1u << 10);
     const uint32_t p0 = kP[0], p1 = kP[1];
-    const unsigned long long P = (unsigned long long)p0 * p1;
-    const unsigned long long Phalf = P >> 1;
 
 #pragma unroll 1
     for (int i = 0; i < kn; ++i) {
@@ -420,9 +438,9 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
                     if (src >= (uint32_t)kN) v = 0u - v;
                     const uint32_t y = v - a[k] + kOff;
                     const int sh = 8 * (m & 3), w = m >> 2;
-                    packed[(0 * 2 + q) * 8 + w] |= ((y >> 25) & 127u) << sh;
-                    packed[(1 * 2 + q) * 8 + w] |= ((y >> 18) & 127u) << sh;
-                    packed[(2 * 2 + q) * 8 + w] |= ((y >> 11) & 127u) << sh;
+                    packed[(0 * 2 + q) * 8 + w] |= field7(y, 25, sh);
+                    packed[(1 * 2 + q) * 8 + w] |= field7(y, 18, sh);
+                    packed[(2 * 2 + q) * 8 + w] |= field7(y, 11, sh);
                 }
             }
             tmem_st16(tdig, packed);
@@ -435,25 +453,36 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 #pragma unroll 1
         for (int pi = 0; pi < 2; ++pi) {
             const uint32_t p = pi ? p1 : p0;
+            const uint32_t pinv = pi ? 9u : 25u;                      // floor(2^32 / p)
             uint32_t a0[32], a1[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) { a0[t] = 0u; a1[t] = 0u; }
+            uint32_t dw[8];
+            tmem_ld8(tdig, dw);
 #pragma unroll 1
             for (int r = 0; r < kRows; ++r) {
-                uint32_t x[32], dw[8];
-                tmem_ld8(tdig + 8 * r, dw);
+                uint32_t x[32];
 #pragma unroll
-                for (int t = 0; t < 32; ++t) x[t] = ((dw[t >> 2] >> (8 * (t & 3))) & 0xFFu) - 64u + p;   // digit mod p
+                for (int t = 0; t < 32; ++t) x[t] = __byte_perm(dw[t >> 2], 0u, 0x4440u | (t & 3)) + (p - 64u);   // digit mod p
+                // the next row's digits arrive while this row is transformed
+                if (r + 1 < kRows) tmem_ld8_async(tdig + 8 * (r + 1), dw);
                 ntt_fwd(x, pi, xch, lane, S.twl[pi][0]);
                 const int c = (i * 2 + pi) * kRows + r;               // chunk of the key stream
                 const int slot = c % kRing;
                 mbar_wait(&S.full[slot], (uint32_t)((c / kRing) & 1), err);
                 const uint4 *kv = reinterpret_cast<const uint4 *>(S.ring[slot]) + lane;   // (w0, w0', w1, w1')
+                // Lazy accumulation: each product is below 2p, so the sums stay
+                // below 12 p0 < 2^32 over all six rows for p0; for p1 (9 p1 > 2^32)
+                // they are brought back below 2p after four rows (8 p1 < 2^32).
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const uint4 v = kv[32 * t];
-                    a0[t] = red2(a0[t] + mul_shoup(x[t], v.x, v.y, p), 2 * p);
-                    a1[t] = red2(a1[t] + mul_shoup(x[t], v.z, v.w, p), 2 * p);
+                    a0[t] += mul_shoup(x[t], v.x, v.y, p);
+                    a1[t] += mul_shoup(x[t], v.z, v.w, p);
+                }
+                if (pi == 1 && r == 3) {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) { a0[t] = red_shoup(a0[t], pinv, p); a1[t] = red_shoup(a1[t], pinv, p); }
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -463,7 +492,10 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
                         load_chunk(S.ring[slot], bkhat + (size_t)(c + kRing) * kChunkWords, &S.full[slot]);
                 }
                 __syncwarp();
+                tmem_wait_ld();
             }
+#pragma unroll
+            for (int t = 0; t < 32; ++t) { a0[t] = red_shoup(a0[t], pinv, p); a1[t] = red_shoup(a1[t], pinv, p); }
             ntt_inv2(a0, a1, pi, xch, lane, S.twl[pi][1]);
             if (pi == 0) {
 #pragma unroll
@@ -472,7 +504,11 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
                 tmem_st32(tres + 32, a1);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             } else {
-                // CRT: v = x0 + p0 * ((x1 - x0) p0^-1 mod p1), lifted to (-P/2, P/2], taken mod 2^32.
+                // CRT: v = x0 + p0 * t, t = (x1 - x0) p0^-1 mod p1, is the product
+                // coefficient in [0, P).  Its exact value has magnitude below
+                // 6 * N * 64 * 2^32 < 2^50.6, far from P / 2 = 2^55.1, so it is
+                // negative exactly when t > p1 / 2, and then v - P is taken.
+                // Only v mod 2^32 is needed.
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     uint32_t x0v[32];
@@ -480,11 +516,10 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 #pragma unroll
                     for (int t = 0; t < 32; ++t) {
                         const int k = lane + 32 * t;
-                        const uint32_t x0 = x0v[t];
-                        const uint32_t x1 = red2(j ? a1[t] : a0[t], p1);
+                        const uint32_t x0 = x0v[t];                       // < p0
+                        const uint32_t x1 = j ? a1[t] : a0[t];            // < 2 p1
                         const uint32_t tq = red2(mul_shoup(x1 - x0 + p1, cP.crt_inv, cP.crt_inv_s, p1), p1);
-                        const unsigned long long v = (unsigned long long)x0 + (unsigned long long)p0 * tq;
-                        const uint32_t lo = (uint32_t)v - (v > Phalf ? (uint32_t)P : 0u);
+                        const uint32_t lo = x0 + p0 * tq - (tq > (p1 >> 1) ? kPmod32 : 0u);
                         acc[j * kN + k] += lo;
                     }
                 }
@@ -520,7 +555,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 // (step, prime, row).
 __global__ void __launch_bounds__(128) bk_ntt_kernel(const uint32_t *__restrict__ bk, uint32_t *__restrict__ out)
 {
-    __shared__ uint32_t xch[4][kXch];
+    __shared__ __align__(16) uint32_t xch[4][kXch];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t id = (size_t)blockIdx.x * 4 + warp;       // ((i * 2 + pi) * 6 + r) * 2 + j
     if (id >= (size_t)kChunks * 2) return;
@@ -587,10 +622,11 @@ int upload_tables()
     }
     pc.crt_inv = powmod(kP[0], kP[1] - 2, kP[1]);
     pc.crt_inv_s = (uint32_t)(((uint64_t)pc.crt_inv << 32) / kP[1]);
-    if (cudaMemcpyToSymbol(cW, W, sizeof W) != cudaSuccess) return -1;
-    if (cudaMemcpyToSymbol(cWs, Ws, sizeof Ws) != cudaSuccess) return -1;
-    if (cudaMemcpyToSymbol(gW, W, sizeof W) != cudaSuccess) return -1;
-    if (cudaMemcpyToSymbol(gWs, Ws, sizeof Ws) != cudaSuccess) return -1;
+    static uint2 Wp[2][2][kN];
+    for (int pi = 0; pi < 2; ++pi)
+        for (int d = 0; d < 2; ++d)
+            for (int k = 0; k < kN; ++k) Wp[pi][d][k] = make_uint2(W[pi][d][k], Ws[pi][d][k]);
+    if (cudaMemcpyToSymbol(cWp, Wp, sizeof Wp) != cudaSuccess) return -1;
     static uint2 WL[2][2][kTwLane];
     for (int pi = 0; pi < 2; ++pi)
         for (int L = 0; L < 32; ++L) {
