@@ -4,15 +4,18 @@
 // Per step i the product out_j = sum_r D_r(X) * BK_i[r][j](X) mod (X^N+1) is an
 // integer polynomial whose coefficients are bounded by 6 * N * 64 * 2^32 <
 // 2^50.6 in magnitude (digits |d| <= 64, key words < 2^32).  It is computed
-// modulo p0 = 167772161 and p1 = 469762049 (both 1 mod 2N, below 2^29) with
-// negacyclic NTTs, recombined by the Chinese remainder theorem into the exact
-// signed integer (p0 * p1 > 2^56), and reduced mod 2^32: bit-identical to the
+// modulo p0 = 167772161 and p1 = 195198977 (both 1 mod 2N) with negacyclic
+// NTTs, recombined by the Chinese remainder theorem into the exact signed
+// integer (p0 * p1 > 2^54.8), and reduced mod 2^32: bit-identical to the
 // dense contraction.
 //
 // Transform: Cooley-Tukey forward / Gentleman-Sande inverse with the powers of
 // a primitive 2N-th root psi in bit-reversed order (the merged negacyclic
-// form), Shoup multiplications with lazy reduction: forward values stay below
-// 8p < 2^32 and are reduced only every other stage.
+// form), Shoup multiplications with lazy reduction.  Both primes are below
+// 2^32 / 22, so a forward value, which grows by less than 2p per stage from
+// below 2p, stays below 22p < 2^32 through all ten stages with no reduction,
+// six pointwise products (each below 2p) sum to less than 12p, and the
+// inverse reduces only on every third stage.
 // The pointwise products are Shoup multiplications by the transformed key,
 // stored with N^-1 folded in and with each value's Shoup companion.
 //
@@ -39,8 +42,8 @@ constexpr int kMaxWarps = 12;
 constexpr int kTwLane = 31 * 32;               // lane-dependent twiddles of one transform: 31 groups x 32 lanes
 constexpr uint32_t kTmemCols = 512;            // per CTA: up to 3 warps share a 32-lane quarter, 112 columns each
 constexpr uint32_t kTmemWarpCols = 112;        // per warp: 64 for the product mod p0, 48 for the packed digits
-constexpr uint32_t kP[2] = {167772161u, 469762049u};   // p0 < p1: the CRT below relies on it
-constexpr uint32_t kPmod32 = (uint32_t)(167772161ull * 469762049ull);   // p0 p1 mod 2^32
+constexpr uint32_t kP[2] = {167772161u, 195198977u};   // p0 < p1 < 2^32 / 22: the bounds below rely on it
+constexpr uint32_t kPmod32 = (uint32_t)(167772161ull * 195198977ull);   // p0 p1 mod 2^32
 constexpr int kXch = 32 * 32;                  // transpose tile (16-byte chunks XOR-swizzled by row)
 constexpr int kChunkWords = 4 * kN;            // one (step, prime, row): per output component the values and their Shoup companions, 16 KB
 constexpr int kChunks = kn * 2 * kRows;        // consumed in this order: step, prime, row
@@ -228,25 +231,25 @@ __device__ __forceinline__ uint32_t field7(uint32_t y, int s, int b)
     return (s >= b ? (y >> (s - b)) : (y << (b - s))) & (127u << b);
 }
 
-// Cooley-Tukey butterfly.  kReduce: inputs below 8p, X first brought below
-// 4p (one conditional subtraction of 4p), outputs below 6p.  Otherwise:
-// inputs below 6p, outputs below 8p.  With p < 2^29 every value fits in 32
-// bits, so stages alternate and half of them skip the reduction.
-template <bool kReduce>
+// Cooley-Tukey butterfly without reduction: t = w Y mod p is below 2p, so
+// outputs exceed the inputs' bound by less than 2p.
 __device__ __forceinline__ void bf_fwd(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
 {
-    const uint32_t x = kReduce ? red2(X, 4 * p) : X;
+    const uint32_t x = X;
     const uint32_t t = mul_shoup(Y, w, ws, p);
     X = x + t;
     Y = x - t + 2 * p;
 }
 
-// Gentleman-Sande butterfly, inputs and outputs below 2p.
-__device__ __forceinline__ void bf_inv(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p)
+// Gentleman-Sande butterfly of inverse stage k, inputs below B = 2p << (k mod 3):
+// Y = w (x - y) mod p below 2p; X = x + y below 2B, brought back below 2p on
+// every third stage (k mod 3 == 2, where 2B = 16p).
+template <int k>
+__device__ __forceinline__ void bf_inv(uint32_t &X, uint32_t &Y, uint32_t w, uint32_t ws, uint32_t p, uint32_t pinv)
 {
     const uint32_t x = X, y = Y;
-    X = red2(x + y, 2 * p);
-    Y = mul_shoup(x - y + 2 * p, w, ws, p);
+    X = (k % 3 == 2) ? red_shoup(x + y, pinv, p) : x + y;
+    Y = mul_shoup(x - y + ((2 * p) << (k % 3)), w, ws, p);
 }
 
 // 32x32 transpose of a warp's registers through shared memory: lane L's x[t]
@@ -267,7 +270,7 @@ __device__ __forceinline__ void transpose32(uint32_t (&x)[32], uint32_t *m, int 
 }
 
 // Forward negacyclic NTT mod kP[pi] of one polynomial: column layout in
-// (values below 2p), row layout out (transform order), values below 6p.  Every loop has a
+// (values below 2p), row layout out (transform order), values below 22p.  Every loop has a
 // compile-time trip count and every array index is a compile-time constant,
 // so the 32 points stay in registers.
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane, const uint2 *twl)
@@ -282,8 +285,7 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
             const int t = (b / dt) * 2 * dt + (b % dt);
             const int k = (1 << s) + (t >> (5 - s));
             const uint2 w = cw[k];
-            if (s & 1) bf_fwd<true>(x[t], x[t + dt], w.x, w.y, p);   // stage 0 inputs are below 2p
-            else bf_fwd<false>(x[t], x[t + dt], w.x, w.y, p);
+            bf_fwd(x[t], x[t + dt], w.x, w.y, p);
         }
     }
     transpose32(x, xch, lane);
@@ -296,47 +298,65 @@ __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch
             const int g = b / dt;                                  // group of this lane's points
             const int t = g * 2 * dt + (b % dt);
             const uint2 w = twl[base + g * 32 + lane];
-            if (s & 1) bf_fwd<true>(x[t], x[t + dt], w.x, w.y, p);
-            else bf_fwd<false>(x[t], x[t + dt], w.x, w.y, p);
+            bf_fwd(x[t], x[t + dt], w.x, w.y, p);
         }
     }
 }
 
 // Inverse negacyclic NTT mod kP[pi] of two polynomials at once: row layout
-// (transform order) in, column layout out (natural order), values below 2p;
-// the N^-1 scaling is folded into the key.
+// (transform order) in, values below 2p; column layout out (natural order),
+// values below 4p.  The N^-1 scaling is folded into the key.
+template <int k>
+__device__ __forceinline__ void inv_stage_in_lane(uint32_t (&a)[32], uint32_t (&c)[32], const uint2 *twl, int lane,
+                                                  uint32_t p, uint32_t pinv)
+{
+    constexpr int dt = 1 << k;
+    constexpr int base = 32 * (32 - (32 >> k));                    // groups of the earlier stages: 16, 8, 4, 2
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const int g = b / dt;
+        const int t = g * 2 * dt + (b % dt);
+        const uint2 w = twl[base + g * 32 + lane];
+        bf_inv<k>(a[t], a[t + dt], w.x, w.y, p, pinv);
+        bf_inv<k>(c[t], c[t + dt], w.x, w.y, p, pinv);
+    }
+}
+
+template <int k>
+__device__ __forceinline__ void inv_stage_uniform(uint32_t (&a)[32], uint32_t (&c)[32], const uint2 *cw, uint32_t p,
+                                                  uint32_t pinv)
+{
+    constexpr int dt = 1 << (k - 5);
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const int t = (b / dt) * 2 * dt + (b % dt);
+        const int idx = (512 >> k) + (t >> (k - 4));
+        const uint2 w = cw[idx];
+        bf_inv<k>(a[t], a[t + dt], w.x, w.y, p, pinv);
+        bf_inv<k>(c[t], c[t + dt], w.x, w.y, p, pinv);
+    }
+}
+
 __device__ __forceinline__ void ntt_inv2(uint32_t (&a)[32], uint32_t (&c)[32], int pi, uint32_t *xch, int lane,
                                          const uint2 *twl)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {            // distance 1 << k: within a lane
-        const int dt = 1 << k;
-        const int base = 32 * (32 - (32 >> k));                  // groups of the earlier stages: 16, 8, 4, 2
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            const int g = b / dt;
-            const int t = g * 2 * dt + (b % dt);
-            const uint2 w = twl[base + g * 32 + lane];
-            bf_inv(a[t], a[t + dt], w.x, w.y, p);
-            bf_inv(c[t], c[t + dt], w.x, w.y, p);
-        }
-    }
+    const uint32_t pinv = pi ? 22u : 25u;                       // floor(2^32 / p)
+    // distance 1 << k: within a lane
+    inv_stage_in_lane<0>(a, c, twl, lane, p, pinv);
+    inv_stage_in_lane<1>(a, c, twl, lane, p, pinv);
+    inv_stage_in_lane<2>(a, c, twl, lane, p, pinv);
+    inv_stage_in_lane<3>(a, c, twl, lane, p, pinv);
+    inv_stage_in_lane<4>(a, c, twl, lane, p, pinv);
     transpose32(a, xch, lane);
     transpose32(c, xch, lane);
+    // distance 32 << (k - 5): within a lane after the transpose
     const uint2 *cw = &cWp[pi][1][0];
-#pragma unroll
-    for (int k = 5; k < 10; ++k) {           // distance 32 << (k-5): within a lane
-        const int dt = 1 << (k - 5);
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            const int t = (b / dt) * 2 * dt + (b % dt);
-            const int idx = (512 >> k) + (t >> (k - 4));
-            const uint2 w = cw[idx];
-            bf_inv(a[t], a[t + dt], w.x, w.y, p);
-            bf_inv(c[t], c[t + dt], w.x, w.y, p);
-        }
-    }
+    inv_stage_uniform<5>(a, c, cw, p, pinv);
+    inv_stage_uniform<6>(a, c, cw, p, pinv);
+    inv_stage_uniform<7>(a, c, cw, p, pinv);
+    inv_stage_uniform<8>(a, c, cw, p, pinv);
+    inv_stage_uniform<9>(a, c, cw, p, pinv);
 }
 
 // CTA c takes jobs [c * per, c * per + per) (per <= WARPS); its other warps idle.
@@ -453,7 +473,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 #pragma unroll 1
         for (int pi = 0; pi < 2; ++pi) {
             const uint32_t p = pi ? p1 : p0;
-            const uint32_t pinv = pi ? 9u : 25u;                      // floor(2^32 / p)
+            const uint32_t pinv = pi ? 22u : 25u;                     // floor(2^32 / p)
             uint32_t a0[32], a1[32];
 #pragma unroll
             for (int t = 0; t < 32; ++t) { a0[t] = 0u; a1[t] = 0u; }
@@ -471,18 +491,13 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
                 const int slot = c % kRing;
                 mbar_wait(&S.full[slot], (uint32_t)((c / kRing) & 1), err);
                 const uint4 *kv = reinterpret_cast<const uint4 *>(S.ring[slot]) + lane;   // (w0, w0', w1, w1')
-                // Lazy accumulation: each product is below 2p, so the sums stay
-                // below 12 p0 < 2^32 over all six rows for p0; for p1 (9 p1 > 2^32)
-                // they are brought back below 2p after four rows (8 p1 < 2^32).
+                // Lazy accumulation: each product is below 2p, the six-row sums
+                // below 12p < 2^32.
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const uint4 v = kv[32 * t];
                     a0[t] += mul_shoup(x[t], v.x, v.y, p);
                     a1[t] += mul_shoup(x[t], v.z, v.w, p);
-                }
-                if (pi == 1 && r == 3) {
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) { a0[t] = red_shoup(a0[t], pinv, p); a1[t] = red_shoup(a1[t], pinv, p); }
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -499,16 +514,20 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
             ntt_inv2(a0, a1, pi, xch, lane, S.twl[pi][1]);
             if (pi == 0) {
 #pragma unroll
-                for (int t = 0; t < 32; ++t) { a0[t] = red2(a0[t], p); a1[t] = red2(a1[t], p); }
+                for (int t = 0; t < 32; ++t) {
+                    a0[t] = red2(red_shoup(a0[t], pinv, p), p);
+                    a1[t] = red2(red_shoup(a1[t], pinv, p), p);
+                }
                 tmem_st32(tres, a0);
                 tmem_st32(tres + 32, a1);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             } else {
                 // CRT: v = x0 + p0 * t, t = (x1 - x0) p0^-1 mod p1, is the product
                 // coefficient in [0, P).  Its exact value has magnitude below
-                // 6 * N * 64 * 2^32 < 2^50.6, far from P / 2 = 2^55.1, so it is
-                // negative exactly when t > p1 / 2, and then v - P is taken.
-                // Only v mod 2^32 is needed.
+                // 6 * N * 64 * 2^32 < 2^50.6, so t < 2^50.6 / p0 < 2^23.3 when it
+                // is non-negative and t > p1 - 2^23.3 when it is negative: it is
+                // negative exactly when t > p1 / 2 (2^26.5), and then v - P is
+                // taken.  Only v mod 2^32 is needed.
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     uint32_t x0v[32];
@@ -517,7 +536,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
                     for (int t = 0; t < 32; ++t) {
                         const int k = lane + 32 * t;
                         const uint32_t x0 = x0v[t];                       // < p0
-                        const uint32_t x1 = j ? a1[t] : a0[t];            // < 2 p1
+                        const uint32_t x1 = j ? a1[t] : a0[t];            // < 4 p1: x1 - x0 + p1 < 2^32
                         const uint32_t tq = red2(mul_shoup(x1 - x0 + p1, cP.crt_inv, cP.crt_inv_s, p1), p1);
                         const uint32_t lo = x0 + p0 * tq - (tq > (p1 >> 1) ? kPmod32 : 0u);
                         acc[j * kN + k] += lo;

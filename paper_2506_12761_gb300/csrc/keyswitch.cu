@@ -6,8 +6,9 @@
 // abar_i = a'_i + 2^15, split into 8 base-4 digits d_ij (j = 0 most
 // significant), and out = (0, b') - sum_{i,j: d_ij != 0} KSK[i][j][d_ij].
 // It is a gather-sum bound by memory bandwidth: a CTA owns 8 or 16 gates and
-// streams each selected 2,528-byte KSK row once for all of them, every
-// thread owning one 16-byte column of the padded 632-word row.
+// streams the 2,528-byte KSK rows of digits 1..3 once for all of them (digit 0
+// selects nothing), every thread owning one 16-byte column of the padded
+// 632-word row.
 #include "vp_internal.h"
 
 namespace vp {
@@ -54,19 +55,29 @@ key_switch_kernel(const KsJob *__restrict__ jobs, int njobs, const uint32_t *__r
 #pragma unroll
     for (int b = 0; b < KS_JOBS; ++b) acc[b] = make_uint4(0u, 0u, 0u, 0u);
 
+    // Per (i, j) the three candidate rows d = 1, 2, 3 are loaded once,
+    // unconditionally and for all eight levels before any is used, so each
+    // thread keeps 24 independent 16-byte loads in flight; every gate then
+    // subtracts the row its digit selects (a CTA-uniform branch: the digits
+    // come from shared memory).
 #pragma unroll 1
     for (int i = 0; i < kN; ++i) {
         uint32_t t[KS_JOBS];
 #pragma unroll
         for (int b = 0; b < KS_JOBS; ++b) t[b] = top[b][i];
         const uint4 *rows = ksk + (size_t)i * kKsT * kKsBase * kKskQuads + c;
+        uint4 r[kKsT][kKsBase - 1];
+#pragma unroll
+        for (int j = 0; j < kKsT; ++j)
+#pragma unroll
+            for (int d = 1; d < kKsBase; ++d) r[j][d - 1] = __ldg(rows + (size_t)(j * kKsBase + d) * kKskQuads);
 #pragma unroll
         for (int j = 0; j < kKsT; ++j) {
 #pragma unroll
             for (int b = 0; b < KS_JOBS; ++b) {
                 const uint32_t d = (t[b] >> (14 - 2 * j)) & 3u;
                 if (d) {
-                    const uint4 v = __ldg(rows + (size_t)(j * kKsBase + d) * kKskQuads);
+                    const uint4 v = d == 1u ? r[j][0] : (d == 2u ? r[j][1] : r[j][2]);
                     acc[b].x -= v.x;
                     acc[b].y -= v.y;
                     acc[b].z -= v.z;
