@@ -302,13 +302,18 @@ def main():
     else:
         kernel_src = "br_ntt.cu"
         from paper_2506_12761_gb300 import ntt_model
-        achieved = (u_br * ntt_model.IMAD_OPS_PER_BOOTSTRAP) / (ms_br / 1e3) / 1e12
+        # a high-half multiply holds the 64-lane IMAD pipe for two slots (measured; see ntt_model)
+        achieved = (u_br * ntt_model.IMAD_SLOTS_PER_BOOTSTRAP) / (ms_br / 1e3) / 1e12
         peak = 152 * 64 * sm_max * 1e6 / 1e12
-        unit = "T int32-multiply ops/s"
+        unit = "T IMAD lane-slots/s"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": traffic_for(kernel_src),
                 "kernel": kernel_src.replace(".cu", ""), "launches": n_br, "avg_launch_ms": ms_br / max(1, n_br),
                 "peak_basis": "152 SMs x 64 int32 multiply lanes/clk x max SM clock %.0f MHz" % sm_max,
+                "work_per_bootstrap": ({"imad_slots": ntt_model.IMAD_SLOTS_PER_BOOTSTRAP,
+                                        "multiplies": ntt_model.IMAD_OPS_PER_BOOTSTRAP,
+                                        "slot_rule": "low-half multiply 1 slot, high-half multiply 2 slots"}
+                                       if args.path == "ntt" else {"int32_macs": MACS_DENSE}),
                 "key_switch": {"launches": n_ks, "avg_launch_ms": ms_ks / max(1, n_ks),
                                "share_of_step": ms_ks / max(1e-9, sum(per_step))}}
 

@@ -302,7 +302,7 @@ int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBu
             CU(cudaEventRecord(ea, c->stream));
         }
         if (l.kind == 0) c->launches += launch_br(c, as<BrJob>(dbr) + l.off, l.n);
-        else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), c->stream);
+        else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), as<int>(c->errw), c->stream);
         else c->launches += launch_free(as<FreeJob>(dfr) + l.off, l.n, c->stream);
         CU(cudaGetLastError());
         nvtxRangePop();
@@ -684,7 +684,7 @@ int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void 
         CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    if (configure_br_dense() != 0 || configure_br_ntt() != 0)
+    if (configure_br_dense() != 0 || configure_br_ntt() != 0 || configure_key_switch() != 0)
         return fail(nullptr, VELOPIR_ERR_CUDA, "cannot raise the shared-memory limit of the blind-rotation kernels");
     int rc = ensure(c, c->errw, 256);
     if (rc) { g_create_error = c->err; return rc; }

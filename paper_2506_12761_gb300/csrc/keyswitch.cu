@@ -5,97 +5,184 @@
 // t = 8 levels): each extracted mask word a'_i is rounded to 16 bits,
 // abar_i = a'_i + 2^15, split into 8 base-4 digits d_ij (j = 0 most
 // significant), and out = (0, b') - sum_{i,j: d_ij != 0} KSK[i][j][d_ij].
-// It is a gather-sum bound by memory bandwidth: a CTA owns 8 or 16 gates and
-// streams the 2,528-byte KSK rows of digits 1..3 once for all of them (digit 0
-// selects nothing), every thread owning one 16-byte column of the padded
-// 632-word row.
+//
+// It is a gather-sum.  A CTA owns G gates, one warp each.  For every i the
+// 24 candidate rows KSK[i][j][1..3] (60.7 KB, three contiguous rows per level)
+// are staged into shared memory by bulk asynchronous copies, double-buffered
+// on mbarriers, so each row crosses L2 once per CTA however many of its gates
+// select it.  Each warp then subtracts, per level, the staged row its gate's
+// digit selects: the digit is uniform across the warp, so a digit of 0 skips
+// the level without divergence, and lane L owns the 16-byte columns
+// L + 32m of the 632-word padded row, so the shared-memory reads are
+// conflict-free.  The bound is shared-memory bandwidth: every gate reads
+// about 6,144 selected rows of 2,528 bytes.
 #include "vp_internal.h"
 
 namespace vp {
 namespace {
 
-constexpr int KS_THREADS = 160;  // 158 active 16-byte columns
+constexpr int kKsRows = kKsT * (kKsBase - 1);                  // 24 staged rows per i
+constexpr uint32_t kKsRowBytes = kKskQuads * 16;               // 2,528
+constexpr uint32_t kKsLevelBytes = (kKsBase - 1) * kKsRowBytes; // rows d = 1..3 of one level, contiguous
+constexpr uint32_t kKsStageBytes = kKsRows * kKsRowBytes;      // 60,672
+constexpr int kKsQuadsPerLane = (kKskQuads + 31) / 32;         // 5
 
-// KS_JOBS gates per CTA: 16 reuses each gathered row more; 8 gives small
-// layers enough CTAs to fill the GPU.
-template <int KS_JOBS>
-__global__ void __launch_bounds__(KS_THREADS)
-key_switch_kernel(const KsJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ big,
-                  const uint4 *__restrict__ ksk)
+template <int G> struct __align__(128) KsSmem {
+    uint4 stage[2][kKsRows][kKskQuads];
+    uint16_t top[G][kN];          // 16-bit rounded a'_i: its 8 base-4 digits
+    uint32_t bprime[G];
+    KsJob job[G];
+    unsigned long long full[2];
+};
+
+__device__ __forceinline__ uint32_t ks_smem_u32(const void *p)
 {
-    __shared__ uint16_t top[KS_JOBS][kN];   // 16-bit rounded a'_i: its 8 base-4 digits
-    __shared__ uint32_t bprime[KS_JOBS];
-    __shared__ KsJob sj[KS_JOBS];
-    const int tid = threadIdx.x;
-    const int job0 = blockIdx.x * KS_JOBS;
-    const int nj = min(KS_JOBS, njobs - job0);
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
-    if (tid < KS_JOBS) {
+__device__ __forceinline__ uint64_t ks_global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool ks_try(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(ks_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (kWaitNs); a timeout is recorded in the error word, and once
+// the error word is set a wait that is not already satisfied returns at once.
+__device__ __forceinline__ void ks_wait(unsigned long long *bar, uint32_t parity, int *err)
+{
+    if (ks_try(bar, parity)) return;
+    if (*reinterpret_cast<volatile int *>(err) != kDevOk) return;
+    const uint64_t t0 = ks_global_ns();
+    while (!ks_try(bar, parity)) {
+        if (ks_global_ns() - t0 > kWaitNs) {
+            atomicExch(err, kDevTimeout);
+            return;
+        }
+    }
+}
+
+// Stage the 24 candidate rows of mask word i into buffer `dst` (one thread).
+__device__ __forceinline__ void ks_stage(uint4 (*dst)[kKskQuads], const uint4 *ksk, int i, unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ks_smem_u32(bar)), "r"(kKsStageBytes)
+                 : "memory");
+#pragma unroll 1
+    for (int j = 0; j < kKsT; ++j) {
+        const uint4 *src = ksk + ((size_t)(i * kKsT + j) * kKsBase + 1) * kKskQuads;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                ks_smem_u32(dst[j * (kKsBase - 1)])),
+            "l"(src), "r"(kKsLevelBytes), "r"(ks_smem_u32(bar))
+            : "memory");
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(G * 32, 1)
+key_switch_kernel(const KsJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ big,
+                  const uint4 *__restrict__ ksk, int *err)
+{
+    extern __shared__ unsigned char ks_smem_raw[];
+    KsSmem<G> &S = *reinterpret_cast<KsSmem<G> *>(ks_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int job0 = blockIdx.x * G;
+    const int nj = min(G, njobs - job0);
+
+    if (tid < G) {
         KsJob j{};
         j.e0 = -1;
         j.e1 = -1;
         if (tid < nj) j = jobs[job0 + tid];
-        sj[tid] = j;
+        S.job[tid] = j;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ks_smem_u32(&S.full[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ks_smem_u32(&S.full[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    for (int idx = tid; idx < KS_JOBS * (kN + 1); idx += KS_THREADS) {
+    if (tid == 0) {
+        ks_stage(S.stage[0], ksk, 0, &S.full[0]);
+        ks_stage(S.stage[1], ksk, 1, &S.full[1]);
+    }
+    for (int idx = tid; idx < G * (kN + 1); idx += G * 32) {
         const int b = idx / (kN + 1), i = idx - b * (kN + 1);
-        const KsJob &j = sj[b];
+        const KsJob &j = S.job[b];
         uint32_t a = 0u;
         if (j.e0 >= 0) a = big[(size_t)j.e0 * kBigWords + i];
         if (j.e1 >= 0) a += big[(size_t)j.e1 * kBigWords + i];
-        if (i < kN) top[b][i] = (uint16_t)((a + (1u << 15)) >> 16);
-        else bprime[b] = a + j.cst;
+        if (i < kN) S.top[b][i] = (uint16_t)((a + (1u << 15)) >> 16);
+        else S.bprime[b] = a + j.cst;
     }
     __syncthreads();
-    const int c = tid;
-    if (c >= kKskQuads) return;
 
-    uint4 acc[KS_JOBS];
+    uint4 acc[kKsQuadsPerLane];
 #pragma unroll
-    for (int b = 0; b < KS_JOBS; ++b) acc[b] = make_uint4(0u, 0u, 0u, 0u);
+    for (int m = 0; m < kKsQuadsPerLane; ++m) acc[m] = make_uint4(0u, 0u, 0u, 0u);
+    const bool active = warp < nj;
 
-    // Per (i, j) the three candidate rows d = 1, 2, 3 are loaded once,
-    // unconditionally and for all eight levels before any is used, so each
-    // thread keeps 24 independent 16-byte loads in flight; every gate then
-    // subtracts the row its digit selects (a CTA-uniform branch: the digits
-    // come from shared memory).
 #pragma unroll 1
     for (int i = 0; i < kN; ++i) {
-        uint32_t t[KS_JOBS];
+        const int buf = i & 1;
+        ks_wait(&S.full[buf], (uint32_t)((i >> 1) & 1), err);
+        if (active) {
+            const uint32_t t = S.top[warp][i];
 #pragma unroll
-        for (int b = 0; b < KS_JOBS; ++b) t[b] = top[b][i];
-        const uint4 *rows = ksk + (size_t)i * kKsT * kKsBase * kKskQuads + c;
-        uint4 r[kKsT][kKsBase - 1];
-#pragma unroll
-        for (int j = 0; j < kKsT; ++j)
-#pragma unroll
-            for (int d = 1; d < kKsBase; ++d) r[j][d - 1] = __ldg(rows + (size_t)(j * kKsBase + d) * kKskQuads);
-#pragma unroll
-        for (int j = 0; j < kKsT; ++j) {
-#pragma unroll
-            for (int b = 0; b < KS_JOBS; ++b) {
-                const uint32_t d = (t[b] >> (14 - 2 * j)) & 3u;
+            for (int j = 0; j < kKsT; ++j) {
+                const uint32_t d = (t >> (14 - 2 * j)) & 3u;
                 if (d) {
-                    const uint4 v = d == 1u ? r[j][0] : (d == 2u ? r[j][1] : r[j][2]);
-                    acc[b].x -= v.x;
-                    acc[b].y -= v.y;
-                    acc[b].z -= v.z;
-                    acc[b].w -= v.w;
+                    const uint4 *row = S.stage[buf][j * (kKsBase - 1) + (int)d - 1];
+#pragma unroll
+                    for (int m = 0; m < kKsQuadsPerLane; ++m) {
+                        const int q = lane + 32 * m;
+                        if (q < kKskQuads) {
+                            const uint4 v = row[q];
+                            acc[m].x -= v.x;
+                            acc[m].y -= v.y;
+                            acc[m].z -= v.z;
+                            acc[m].w -= v.w;
+                        }
+                    }
                 }
             }
         }
+        __syncthreads();   // every warp is done with this buffer: refill it
+        if (tid == 0 && i + 2 < kN) ks_stage(S.stage[buf], ksk, i + 2, &S.full[buf]);
     }
+
+    // Copies still in flight after a timed-out wait must land before the
+    // shared memory is released.
+    if (tid == 0 && *reinterpret_cast<volatile int *>(err) != kDevOk) {
+        for (int b = 0; b < 2; ++b)
+            for (uint32_t ph = 0; ph < 2; ++ph) {
+                const uint64_t t0 = ks_global_ns();
+                while (!ks_try(&S.full[b], ph) && ks_global_ns() - t0 <= kWaitNs) {
+                }
+            }
+    }
+    if (!active) return;
+    uint32_t *out = S.job[warp].out;
 #pragma unroll
-    for (int b = 0; b < KS_JOBS; ++b) {
-        if (b >= nj) break;
-        uint32_t *out = sj[b].out;
-        const uint32_t v[4] = {acc[b].x, acc[b].y, acc[b].z, acc[b].w};
+    for (int m = 0; m < kKsQuadsPerLane; ++m) {
+        const int q = lane + 32 * m;
+        const uint32_t v[4] = {acc[m].x, acc[m].y, acc[m].z, acc[m].w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int w = 4 * c + e;
+            const int w = 4 * q + e;
             if (w < kn) out[w] = v[e];
-            else if (w == kn) out[kn] = bprime[b] + v[e];
+            else if (w == kn) out[kn] = S.bprime[warp] + v[e];
         }
     }
 }
@@ -122,7 +209,19 @@ __global__ void pad_ksk_kernel(const uint32_t *__restrict__ src, uint32_t *__res
 
 }  // namespace
 
-int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev,
+int configure_key_switch()
+{
+    if (cudaFuncSetAttribute(key_switch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(KsSmem<8>)) != cudaSuccess)
+        return -1;
+    if (cudaFuncSetAttribute(key_switch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(KsSmem<16>)) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+// 16 gates per CTA stage each row for more gates; 8 when that would leave SMs idle.
+int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev, int *err,
                       cudaStream_t st)
 {
     if (njobs <= 0) return 0;
@@ -134,10 +233,10 @@ int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const u
         if (sms <= 0) sms = 152;
     }
     const uint4 *k4 = reinterpret_cast<const uint4 *>(ksk_dev);
-    if ((njobs + 15) / 16 < 2 * sms)
-        key_switch_kernel<8><<<(njobs + 7) / 8, KS_THREADS, 0, st>>>(jobs, njobs, big, k4);
+    if (njobs < 16 * sms)
+        key_switch_kernel<8><<<(njobs + 7) / 8, 8 * 32, sizeof(KsSmem<8>), st>>>(jobs, njobs, big, k4, err);
     else
-        key_switch_kernel<16><<<(njobs + 15) / 16, KS_THREADS, 0, st>>>(jobs, njobs, big, k4);
+        key_switch_kernel<16><<<(njobs + 15) / 16, 16 * 32, sizeof(KsSmem<16>), st>>>(jobs, njobs, big, k4, err);
     return 1;
 }
 

@@ -126,6 +126,6 @@ extern "C" int velopir_bootstrap_batch_noalloc(velopir_ctx *ctx, velopir_gate ga
     uint64_t launches = 1;
     if (R.bk_ntt) launches += launch_br_ntt(S->br, nrot, R.bk_ntt, S->big, R.err, R.stream);
     else launches += launch_br_dense(S->br, nrot, R.bk, S->big, R.err, R.stream);
-    launches += launch_key_switch(S->ks, n, S->big, R.ksk, R.stream);
+    launches += launch_key_switch(S->ks, n, S->big, R.ksk, R.err, R.stream);
     return ctx_finish(ctx, launches);
 }

@@ -85,7 +85,8 @@ int ntt_pick_warps(int njobs);                 // the tuned choice for a launch 
 void ntt_set_wave_ms(int warps, float ms);     // record a measured full-wave time
 size_t bk_ntt_words();
 
-int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev,
+int configure_key_switch();
+int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev, int *err,
                       cudaStream_t st);
 int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st);
 int launch_pad_ksk(const uint32_t *ksk_abi, uint32_t *ksk_dev, cudaStream_t st);
