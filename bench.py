@@ -2,7 +2,8 @@
 
 One step = one interval-validation query (Alg. InterValid) over D = 1,024
 plaintext rectangles with a 32-bit unsigned encrypted point: 131 bootstraps
-per entry, 134,144 per step, issued as 34 batched layers.  Inputs and keys
+per entry, 134,144 per step: 34 gate layers, list-scheduled into launches
+of whole waves of the blind-rotation kernel.  Inputs and keys
 are synthetic and seeded (paper_2506_12761_gb300.synth), shaped like the
 paper's interval-validation workload.
 
@@ -32,7 +33,8 @@ UNIT = "bootstraps/s"
 D = 1024
 BOOTSTRAPS_PER_STEP = 131 * D
 WORKLOAD = ("interval validation: 32-bit unsigned encrypted point vs D=1024 plaintext rectangles, "
-            "131 bootstraps/entry = 134,144 bootstraps/step in 34 batched layers; TFHE n=630 N=1024 l=3 Bg=2^7 t=8")
+            "131 bootstraps/entry = 134,144 bootstraps/step (34 gate layers, list-scheduled into launches of "
+            "whole waves); TFHE n=630 N=1024 l=3 Bg=2^7 t=8")
 MACS_DENSE = 12 * 1024 * 1024 * 630          # int32 multiply-adds per bootstrap, dense contraction
 
 

@@ -48,7 +48,9 @@ enum {
     VELOPIR_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed */
     VELOPIR_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
     VELOPIR_ERR_BUSY = -6,    /* serving queue full / ticket not finished */
-    VELOPIR_ERR_NOCUDA = -7   /* no CUDA device is visible */
+    VELOPIR_ERR_NOCUDA = -7,  /* no CUDA device is visible */
+    VELOPIR_ERR_PLAN = -8     /* a dry run found a gate reading a value that was
+                                 not yet written or already overwritten */
 };
 
 /* Gates (Section 2.2 names HomAND, HomXOR, HomXNOR; the others are tfhe-2's
@@ -228,6 +230,29 @@ int velopir_autotune(velopir_ctx *ctx, double *wave_ms_out, int n_out);
 /* Bootstraps per CTA the current path would use for a batch of `count`
  * (>= 1 on success).  Errors: ERR_ARG. */
 int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
+
+/* Host-only dry run of a query's launch plan; no GPU or context is used.
+ * Builds the gate program of q (Section 5's circuits for IntV, CoV or IdM,
+ * with q->kind, D, db, id_bits, payload and payload_bits as in the query
+ * calls; enc_a, enc_b and out are ignored), schedules it as the device path
+ * does -- launches of whole waves of `wave` blind rotations when at least a
+ * wave is ready, longest dependency chain first (wave = 0: one launch per
+ * as-soon-as-possible layer) -- assigns pool slots, and executes it on
+ * noiseless plaintext phases instead of ciphertexts: each ciphertext is its
+ * message +-1/8 (Section 2.2 Ecd) and each bootstrap returns the message of
+ * the sign of its pre-combined phase (phase 0 reads as true).
+ *   bits_a: the query's plaintext bits, one uint32_t 0/1 per ciphertext of
+ *           enc_a (IntV x[32], CoV cell[32], IdM id[id_bits]), LSB first;
+ *   bits_b: IntV y[32], else ignored (nullable);
+ *   bits_out: receives one 0/1 per output ciphertext (D entries, or
+ *             payload_bits for IdM with a payload);
+ *   launch_sizes (nullable): receives the blind rotations of each launch,
+ *           up to max_launches entries.
+ * Returns the number of launches (>= 1), VELOPIR_ERR_ARG for bad arguments,
+ * or VELOPIR_ERR_PLAN if any gate of the plan would read a value that is not
+ * yet written or whose pool slot was already reused. */
+int velopir_plan_query(const velopir_query *q, int wave, const uint32_t *bits_a, const uint32_t *bits_b,
+                       uint32_t *bits_out, size_t *launch_sizes, int max_launches);
 
 /* ---- serving: asynchronous queries with continuous batching ------------- */
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvelopir.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "br_dense.cu", "br_ntt.cu", "keyswitch.cu", "sched.cpp", "client.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "br_dense.cu", "br_ntt.cu", "keyswitch.cu", "sched.cpp", "plan.cpp", "client.cpp", "noalloc.cu"]
 
 
 def nvcc() -> str:

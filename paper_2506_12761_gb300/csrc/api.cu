@@ -348,6 +348,7 @@ int run_program(velopir_ctx *c, Program &P, bool graph = false)
 {
     int rc;
     if ((rc = ensure_path_key(c))) return rc;
+    if (c->path == VP_PATH_NTT) relayer(P, ntt_full_wave());
     allocate_slots(P);
     if ((rc = ensure(c, c->pool, std::max<size_t>(1, (size_t)P.nphys) * kSlotWords * 4))) return rc;
     size_t max_br = 1;

@@ -707,6 +707,20 @@ int configure_br_ntt()
 }
 
 int ntt_shape_count() { return 5; }
+
+// Blind rotations in one full wave of the most efficient tuned shape (the
+// least wave time per bootstrap), or 0 before the autotuner has run.
+int ntt_full_wave()
+{
+    const int sms = g_sms > 0 ? g_sms : 152;
+    int best = 0;
+    for (int i = 0; i < (int)(sizeof(kShapes) / sizeof(kShapes[0])); ++i) {
+        const int w = kShapes[i];
+        if (g_wave_ms[w] <= 0) return 0;
+        if (best == 0 || g_wave_ms[w] / w < g_wave_ms[best] / best) best = w;
+    }
+    return sms * best;
+}
 int ntt_shape(int i) { return kShapes[i]; }
 void ntt_set_wave_ms(int warps, float ms) { if (warps >= 1 && warps <= kMaxWarps) g_wave_ms[warps] = ms; }
 

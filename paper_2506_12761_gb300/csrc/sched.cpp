@@ -2,6 +2,8 @@
 #include "sched.h"
 
 #include <algorithm>
+#include <deque>
+#include <unordered_map>
 
 namespace vp {
 
@@ -217,6 +219,132 @@ void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size
             }
     if (D == 1)
         for (int j = 0; j < payload_bits; ++j) B.materialize(S[j], out + (size_t)j * kLweWords);
+}
+
+void relayer(Program &p, int wave)
+{
+    if (wave <= 0 || p.layers.size() <= 1) return;
+    struct G {
+        int layer, ks, nbr, height = 1, indeg = 0, at = -1;
+        std::vector<int> succ;
+    };
+    std::vector<G> g;
+    std::unordered_map<uint64_t, int> producer;   // output address (slot tag or device) -> gate
+    for (int l = 0; l < (int)p.layers.size(); ++l) {
+        const Layer &L = p.layers[l];
+        for (int k = 0; k < (int)L.ks.size(); ++k) {
+            G x;
+            x.layer = l;
+            x.ks = k;
+            x.nbr = L.ks[k].e1 >= 0 ? 2 : 1;
+            producer[(uint64_t)(uintptr_t)L.ks[k].out] = (int)g.size();
+            g.push_back(std::move(x));
+        }
+        // a free job's output is ready with its input's producer
+        for (const FreeJob &f : L.fr) {
+            auto it = f.in ? producer.find((uint64_t)(uintptr_t)f.in) : producer.end();
+            if (it != producer.end()) producer[(uint64_t)(uintptr_t)f.out] = it->second;
+        }
+    }
+    const int ng = (int)g.size();
+    for (int i = 0; i < ng; ++i) {
+        const Layer &L = p.layers[g[i].layer];
+        const KsJob &k = L.ks[g[i].ks];
+        int preds[4], np = 0;
+        for (int e : {k.e0, k.e1}) {
+            if (e < 0) continue;
+            for (const uint32_t *in : {L.br[e].in0, L.br[e].in1}) {
+                if (!in) continue;
+                auto it = producer.find((uint64_t)(uintptr_t)in);
+                if (it == producer.end() || it->second == i) continue;
+                bool dup = false;
+                for (int q = 0; q < np; ++q) dup |= preds[q] == it->second;
+                if (!dup) preds[np++] = it->second;
+            }
+        }
+        for (int q = 0; q < np; ++q) {
+            g[preds[q]].succ.push_back(i);
+            g[i].indeg++;
+        }
+    }
+    // longest chain of gates from each gate to the end (producers precede
+    // consumers in the ASAP order, so a reverse sweep sees successors first)
+    int hmax = 1;
+    for (int i = ng - 1; i >= 0; --i) {
+        for (int s : g[i].succ) g[i].height = std::max(g[i].height, 1 + g[s].height);
+        hmax = std::max(hmax, g[i].height);
+    }
+    std::vector<std::deque<int>> ready(hmax + 1);
+    size_t nready = 0;
+    for (int i = 0; i < ng; ++i)
+        if (g[i].indeg == 0) { ready[g[i].height].push_back(i); nready += g[i].nbr; }
+    std::vector<std::vector<int>> sched;
+    std::vector<int> next;
+    int done = 0;
+    while (done < ng) {
+        const size_t cap = nready >= (size_t)wave ? nready / wave * wave : nready;
+        std::vector<int> take;
+        size_t used = 0;
+        for (int h = hmax; h >= 1 && used < cap; --h) {
+            auto &q = ready[h];
+            while (!q.empty() && used + g[q.front()].nbr <= cap) {
+                take.push_back(q.front());
+                used += g[q.front()].nbr;
+                q.pop_front();
+            }
+        }
+        if (take.empty())   // only a two-rotation gate is ready and cap is odd: take it anyway
+            for (int h = hmax; h >= 1 && take.empty(); --h)
+                if (!ready[h].empty()) { take.push_back(ready[h].front()); used += g[take[0]].nbr; ready[h].pop_front(); }
+        nready -= used;
+        const int t = (int)sched.size();
+        next.clear();
+        for (int i : take) {
+            g[i].at = t;
+            for (int s : g[i].succ)
+                if (--g[s].indeg == 0) next.push_back(s);
+        }
+        for (int s : next) { ready[g[s].height].push_back(s); nready += g[s].nbr; }
+        done += (int)take.size();
+        sched.push_back(std::move(take));
+    }
+
+    // rebuild the layers, the free jobs after their producer's layer, and slot liveness
+    std::vector<std::vector<FreeJob>> fr_of(ng);
+    for (const Layer &L : p.layers)
+        for (const FreeJob &f : L.fr) {
+            auto it = f.in ? producer.find((uint64_t)(uintptr_t)f.in) : producer.end();
+            if (it != producer.end()) fr_of[it->second].push_back(f);
+            else p.pre.push_back(f);
+        }
+    std::vector<Layer> NL(sched.size());
+    for (size_t t = 0; t < sched.size(); ++t)
+        for (int i : sched[t]) {
+            const Layer &L = p.layers[g[i].layer];
+            KsJob k = L.ks[g[i].ks];
+            const int e0 = (int)NL[t].br.size();
+            NL[t].br.push_back(L.br[k.e0]);
+            if (k.e1 >= 0) NL[t].br.push_back(L.br[k.e1]);
+            k.e0 = e0;
+            k.e1 = k.e1 >= 0 ? e0 + 1 : -1;
+            NL[t].ks.push_back(k);
+            for (const FreeJob &f : fr_of[i]) NL[t].fr.push_back(f);
+        }
+    p.layers.swap(NL);
+    auto slot_of = [](const void *a) { return ((uint64_t)(uintptr_t)a & kSlotTag) ? (int)((uint64_t)(uintptr_t)a & ~kSlotTag) : -1; };
+    for (int l = 0; l < (int)p.layers.size(); ++l) {
+        const Layer &L = p.layers[l];
+        for (const KsJob &k : L.ks)
+            if (int v = slot_of(k.out); v >= 0) p.slot_def[v] = p.slot_last[v] = l;
+    }
+    for (int l = 0; l < (int)p.layers.size(); ++l) {
+        const Layer &L = p.layers[l];
+        for (const BrJob &j : L.br)
+            for (const uint32_t *in : {j.in0, j.in1})
+                if (int v = in ? slot_of(in) : -1; v >= 0) p.slot_last[v] = std::max(p.slot_last[v], l);
+        for (const FreeJob &f : L.fr)
+            if (int v = f.in ? slot_of(f.in) : -1; v >= 0) p.slot_last[v] = std::max(p.slot_last[v], l);
+    }
 }
 
 void allocate_slots(Program &p)

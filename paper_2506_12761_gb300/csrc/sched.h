@@ -77,6 +77,16 @@ void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uin
 void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
                int payload_bits, uint32_t *out);
 
+// Wave-filling list schedule (replaces the as-soon-as-possible layers of a
+// built program, before allocate_slots).  A gate may run in any launch after
+// the launches of the gates it reads; each launch takes, among the ready
+// gates, a whole number of full waves (`wave` blind rotations) when at least
+// one wave is ready (otherwise everything ready), choosing gates with the
+// longest remaining dependency chain first.  The rest waits and merges with
+// the gates that become ready.  Results are unchanged (every gate computes
+// the same function of the same inputs); wave <= 0 keeps the ASAP layers.
+void relayer(Program &p, int wave);
+
 // Liveness-based assignment of virtual slots to physical pool slots: a slot is
 // reused only in a layer after the last layer that reads its previous value.
 void allocate_slots(Program &p);

@@ -83,6 +83,7 @@ int ntt_shape_count();                         // tile shapes of the NTT kernel 
 int ntt_shape(int i);                          // the i-th shape, ascending
 int ntt_pick_warps(int njobs);                 // the tuned choice for a launch of njobs
 void ntt_set_wave_ms(int warps, float ms);     // record a measured full-wave time
+int ntt_full_wave();                           // bootstraps in one full wave of the best tuned shape (0: untuned)
 size_t bk_ntt_words();
 
 int configure_key_switch();

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libvelopir.so")
 
 VELOPIR_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_NOKEY", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_BUSY",
-          -7: "ERR_NOCUDA"}
+          -7: "ERR_NOCUDA", -8: "ERR_PLAN"}
 (VP_AND, VP_NAND, VP_OR, VP_NOR, VP_XOR, VP_XNOR, VP_ANDNY, VP_ANDYN, VP_ORNY, VP_ORYN, VP_MUX) = range(11)
 VP_PATH_INT32_DENSE, VP_PATH_NTT, VP_PATH_TENSOR_F16 = 0, 1, 2
 VP_QUERY_INTV, VP_QUERY_COV, VP_QUERY_IDM = 0, 1, 2
@@ -35,7 +35,7 @@ EXPORTS = [
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
-    "velopir_selftest_wait_timeout",
+    "velopir_selftest_wait_timeout", "velopir_plan_query",
 ]
 NOALLOC_MAX_GATES = 256
 NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
             "velopir_graph_replays": (u64, [vp]),
             "velopir_autotune": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
             "velopir_tuned_shape": (i, [vp, sz]),
+            "velopir_plan_query": (i, [ctypes.POINTER(Query), i, vp, vp, vp, ctypes.POINTER(sz), i]),
             "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(ctypes.c_double)]),
         }
@@ -313,3 +314,24 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0, id_bits: int = 0,
+                       payload=None, payload_bits: int = 0, max_launches: int = 4096):
+    """Host-only dry run of a query's launch plan on plaintext bits.
+
+    Returns (result bits, blind rotations per launch).  Raises VelopirError
+    (ERR_PLAN) if the plan reads a value before it is written or after its
+    pool slot was reused."""
+    db = np.ascontiguousarray(db, dtype=np.uint32)
+    a = np.ascontiguousarray(bits_a, dtype=np.uint32)
+    b = None if bits_b is None else np.ascontiguousarray(bits_b, dtype=np.uint32)
+    pay = None if payload is None else np.ascontiguousarray(payload, dtype=np.uint32)
+    q = Query(kind, id_bits, payload_bits, 0, None, None, ptr(db), ptr(pay), D, None)
+    nout = payload_bits if (kind == VP_QUERY_IDM and payload is not None) else D
+    out = np.zeros(max(1, nout), dtype=np.uint32)
+    sizes = (ctypes.c_size_t * max_launches)()
+    rc = lib().velopir_plan_query(ctypes.byref(q), wave, ptr(a), ptr(b), ptr(out), sizes, max_launches)
+    if rc < 0:
+        raise VelopirError(rc, "velopir_plan_query")
+    return out[:nout], [int(sizes[k]) for k in range(min(rc, max_launches))]

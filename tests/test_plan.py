@@ -1,0 +1,119 @@
+"""The launch scheduler, checked on the CPU through velopir_plan_query.
+
+The dry run executes the scheduled gate program on noiseless plaintext
+phases with the device's pool-slot reuse, so a dependency the scheduler
+breaks (a gate placed in the launch of, or before, a gate it reads) or a
+pool slot reused too early either makes the answer wrong or is reported as
+ERR_PLAN.  Answers are compared with the plaintext predicates of the modes
+(Alg. InterValid, CoV, IdM with HomSum aggregation of Section 5)."""
+import numpy as np
+import pytest
+
+from paper_2506_12761_gb300 import velopir as vp
+
+WAVES = (0, 48, 64, 1824)
+
+
+def bits(v, n):
+    return np.array([(int(v) >> i) & 1 for i in range(n)], dtype=np.uint32)
+
+
+def intv_case(D, seed):
+    rng = np.random.default_rng(seed)
+    u = rng.integers(0, 2**32, size=(D, 4), dtype=np.uint64)
+    lo = np.minimum(u[:, [0, 2]], u[:, [1, 3]])
+    hi = np.maximum(u[:, [0, 2]], u[:, [1, 3]])
+    x, y = (int(v) for v in rng.integers(0, 2**32, size=2, dtype=np.uint64))
+    # plant hits and near misses on the bounds
+    lo[: D // 4, 0], hi[: D // 4, 0] = x, x + 1
+    lo[D // 4: D // 2, 1] = y + 1
+    rects = np.stack([lo[:, 0], hi[:, 0], lo[:, 1], hi[:, 1]], axis=1).astype(np.uint64)
+    rects = np.minimum(rects, 2**32 - 1).astype(np.uint32)
+    r = rects.astype(np.int64)
+    want = ((r[:, 0] <= x) & (x < r[:, 1]) & (r[:, 2] <= y) & (y < r[:, 3])).astype(np.uint32)
+    return rects, bits(x, 32), bits(y, 32), want
+
+
+def launches_are_waves(sizes, wave, total):
+    assert sum(sizes) == total
+    if wave:
+        # a launch is a whole number of waves, or all that was ready when
+        # less than a wave was
+        assert all(s % wave == 0 or s < wave for s in sizes), sizes
+
+
+@pytest.mark.parametrize("wave", WAVES)
+def test_intv_plan_answers_the_predicate(wave):
+    D = 200
+    rects, bx, by, want = intv_case(D, 3)
+    out, sizes = vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, D, bx, by, wave=wave)
+    assert np.array_equal(out, want)
+    assert 0 < want.sum() < D
+    launches_are_waves(sizes, wave, 131 * D)
+
+
+def test_wave_filling_shortens_the_schedule_in_waves():
+    """IntV D = 1,024 at 12 bootstraps per SM: 34 ASAP layers need 2.25 waves
+    each (3 launched waves per 4,096-gate layer); the wave-filled schedule
+    needs 74 waves in total, all full but the last."""
+    D = 1024
+    rects, bx, by, want = intv_case(D, 4)
+    wave = 152 * 12
+    out0, asap = vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, D, bx, by, wave=0)
+    out1, filled = vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, D, bx, by, wave=wave)
+    assert np.array_equal(out0, want) and np.array_equal(out1, want)
+    assert len(asap) == 34 and asap[0] == 4096
+    waves = lambda sizes: sum(-(-s // wave) for s in sizes)
+    assert waves(asap) == 32 * 3 + 2 + 1
+    assert waves(filled) == -(-131 * D // wave) == 74
+
+
+@pytest.mark.parametrize("wave", WAVES)
+def test_cov_plan_answers_equality(wave):
+    rng = np.random.default_rng(5)
+    D = 150
+    cells = rng.integers(0, 2**32, size=D, dtype=np.uint64).astype(np.uint32)
+    q = int(cells[17])
+    cells[60] = q ^ 1          # one bit off in x
+    cells[61] = q ^ (1 << 31)  # one bit off in y
+    out, sizes = vp.velopir_plan_query(vp.VP_QUERY_COV, cells, D, bits(q, 32), wave=wave)
+    assert np.array_equal(out, (cells == q).astype(np.uint32))
+    launches_are_waves(sizes, wave, 31 * D)
+
+
+@pytest.mark.parametrize("wave", WAVES)
+def test_idm_payload_aggregation_plan(wave):
+    rng = np.random.default_rng(6)
+    D = 77
+    ids = rng.choice(2**32, size=D, replace=False).astype(np.uint32)
+    pay = rng.integers(0, 2**32, size=D, dtype=np.uint64).astype(np.uint32)
+    q = int(ids[40])
+    out, sizes = vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, D, bits(q, 32), wave=wave, id_bits=32,
+                                       payload=pay, payload_bits=32)
+    assert np.array_equal(out, bits(pay[40], 32))
+    launches_are_waves(sizes, wave, 31 * D + 32 * (D - 1))
+    miss, _ = vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, D, bits(q ^ 4, 32), wave=wave, id_bits=32,
+                                    payload=pay, payload_bits=32)
+    assert not miss.any() or (q ^ 4) in set(ids.tolist())
+
+
+@pytest.mark.parametrize("id_bits", [1, 5, 8, 32])
+def test_idm_match_bits_plan(id_bits):
+    rng = np.random.default_rng(id_bits)
+    D = 40
+    ids = rng.integers(0, 2**id_bits, size=D, dtype=np.uint64).astype(np.uint32)
+    q = int(ids[3])
+    out, _ = vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, D, bits(q, id_bits), wave=16, id_bits=id_bits)
+    assert np.array_equal(out, (ids == q).astype(np.uint32))
+
+
+def test_plan_rejects_bad_arguments():
+    cells = np.zeros(4, dtype=np.uint32)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_QUERY_COV, cells, 0, bits(0, 32))
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_QUERY_IDM, cells, 4, bits(0, 32), id_bits=33)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_QUERY_INTV, np.zeros((4, 4), np.uint32), 4, bits(0, 32), None)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(7, cells, 4, bits(0, 32))
