@@ -189,6 +189,57 @@ int velopir_coordinate_query(velopir_ctx *ctx, const uint32_t *enc_cell, const u
 int velopir_id_match(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, const uint32_t *ids,
                      size_t D, const uint32_t *payload, int payload_bits, uint32_t *out);
 
+/* ---- encrypted database (the paper's protocol) ----------------------------- */
+
+/* Section 3.2's preprocessing encrypts the database under the client's key:
+ * Alg. PubKeyGen gives the server one fresh encryption of zero per database
+ * bit, Alg. ServerEnc adds the encoded bit to it.  The query then runs
+ * Section 4-5's circuits with both operands encrypted: equality tests
+ * bootstrap their XNORs, comparators their XNORs and MUXes (Alg. HomCompLeOPT:
+ * t0 = XOR of the top bits, t1 = MUX(XNOR(c1_i, c2_i), t1, c2_i) for
+ * i = 0..l-2, result MUX(t0, c1_top, t1); two blind rotations per MUX), and
+ * an encrypted payload is zeroed with a bootstrapped AND (Alg.
+ * HomBitwiseAND).  Ciphertext arrays may be host or device memory; outputs
+ * as in the plaintext-database calls. */
+
+/* Alg. PubKeyGen: count encryptions of zero, pk_i = (a_i, <a_i, s> + e_i).
+ * s: uint32_t[630] (0/1), a: uint32_t[count][630] uniform, e: uint32_t[count]
+ * noise (torus words), pk_out: uint32_t[count][631].  Host only.  Errors: ERR_ARG. */
+int velopir_client_pubkeygen(const uint32_t *s, const uint32_t *a, const uint32_t *e, size_t count,
+                             uint32_t *pk_out);
+
+/* Alg. ServerEnc: ct_i = (0, Ecd(bit_i)) + pk_i (Ecd(1) = 1/8, Ecd(0) = -1/8).
+ * pk: uint32_t[count][631], bits: uint32_t[count] (0/1), ct_out:
+ * uint32_t[count][631].  Host only; uses no secret.  Errors: ERR_ARG. */
+int velopir_server_encrypt(const uint32_t *pk, const uint32_t *bits, size_t count, uint32_t *ct_out);
+
+/* IntV over an encrypted database (Alg. InterValid): out_bits[d] =
+ * Enc(x_lo <= x < x_hi && y_lo <= y < y_hi) for l-bit unsigned coordinates
+ * (1 <= l <= 32; the paper's interval precision l_I).  enc_x, enc_y:
+ * [l][631]; enc_rects: [D][4][l][631] (x_lo, x_hi, y_lo, y_hi, bits LSB
+ * first); out_bits: [D][631].  12 l + 3 bootstraps per entry (per
+ * comparator: 1 XOR, l-1 XNORs, l MUXes of 2).  Errors: ERR_ARG, ERR_NOKEY,
+ * ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
+int velopir_interval_query_encdb(velopir_ctx *ctx, const uint32_t *enc_x, const uint32_t *enc_y, int l,
+                                 const uint32_t *enc_rects, size_t D, uint32_t *out_bits);
+
+/* CoV over an encrypted database (Alg. CoV with Alg. HomEqOPT): enc_cell:
+ * [2w][631] (w bits of x, then w bits of y; 1 <= w <= 16), enc_cells:
+ * [D][2w][631]; out_bits[d] = Enc(cell == cell_d): [D][631].  4 w - 1
+ * bootstraps per entry.  Errors: as above. */
+int velopir_coordinate_query_encdb(velopir_ctx *ctx, const uint32_t *enc_cell, int w, const uint32_t *enc_cells,
+                                   size_t D, uint32_t *out_bits);
+
+/* IdM over an encrypted database: enc_id: [id_bits][631] (1..32 bits),
+ * enc_ids: [D][id_bits][631].  enc_payload == NULL: out = [D][631] match
+ * bits (2 id_bits - 1 bootstraps per entry).  Otherwise enc_payload:
+ * [D][payload_bits][631] (1..32 bits), each zeroed by its entry's match bit
+ * with a bootstrapped AND and XOR-aggregated (Section 5's HomSum): out =
+ * [payload_bits][631], the payload of the matching entry (0 if none).
+ * Errors: as above. */
+int velopir_id_match_encdb(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, const uint32_t *enc_ids,
+                           size_t D, const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+
 /* ---- several queries as one program --------------------------------------- */
 
 typedef enum { VP_QUERY_INTV = 0, VP_QUERY_COV = 1, VP_QUERY_IDM = 2 } velopir_query_kind;

@@ -4,6 +4,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -177,6 +178,16 @@ def encrypt_bits(s, bits, lwe_mat) -> np.ndarray:
     bits = np.asarray(bits).reshape(-1)
     mu = np.where(bits != 0, MU, (1 << 32) - MU).astype(np.uint32)
     return encrypt_mu(s, lwe_mat.a[: len(bits)], lwe_mat.e[: len(bits)], mu)
+
+
+def server_encrypt(pk, bits) -> np.ndarray:
+    """Alg. ServerEnc: ct = (0, Ecd(bit)) + pk for one public-key ciphertext
+    pk (an encryption of zero from Alg. PubKeyGen, i.e. encrypt_mu with mu = 0)
+    per bit; Ecd(1) = 1/8, Ecd(0) = -1/8 (Section 2.2)."""
+    pk = _u32(pk).reshape(-1, _u32(pk).shape[-1]).copy()
+    bits = np.asarray(bits).reshape(-1)
+    pk[:, -1] += np.where(bits != 0, MU, (1 << 32) - MU).astype(np.uint32)
+    return pk
 
 
 def phase(s, ct) -> np.ndarray:
@@ -379,4 +390,76 @@ def idm_payload(keys: Keys, x_cts, ids, payload, payload_bits: int = 32, threads
     for d in range(D):
         for j in range(payload_bits):
             S[d, j] = zero_out_plain(v[d], int((int(pay[d]) >> j) & 1))
+    return homsum_tree(keys, S, threads)
+
+
+# --------------------------------------------------------------------------
+# Encrypted database (Section 3.2: the database bits are ServerEnc ciphertexts)
+# --------------------------------------------------------------------------
+
+def _pool(threads):
+    return ThreadPoolExecutor(max_workers=threads or default_threads())
+
+
+def comp_enc_unsigned(keys: Keys, c1, c2, strict: bool) -> np.ndarray:
+    """c1 <= c2 (strict: c1 < c2) as unsigned l-bit integers: Alg.
+    HomCompLeOPT / HomCompL (comp_enc, signed two's complement) on operands
+    whose top bits are both negated."""
+    c1, c2 = _u32(c1).copy(), _u32(c2).copy()
+    c1[-1] = lwe_not(c1[-1])
+    c2[-1] = lwe_not(c2[-1])
+    return comp_enc(keys, c1, c2, strict)
+
+
+def intv_enc_batch(keys: Keys, cx, cy, enc_rects, threads: int | None = None) -> np.ndarray:
+    """Alg. InterValid with encrypted bounds: AND(AND(LE(x_lo,x), L(x,x_hi)),
+    AND(LE(y_lo,y), L(y,y_hi))).  enc_rects: [D][4][l][n+1] (x_lo, x_hi, y_lo,
+    y_hi).  The four comparators of all entries run on a thread pool."""
+    cx, cy = _u32(cx), _u32(cy)
+    R = _u32(enc_rects)
+    D = R.shape[0]
+    jobs = []
+    for d in range(D):
+        jobs += [(R[d, 0], cx, False), (cx, R[d, 1], True), (R[d, 2], cy, False), (cy, R[d, 3], True)]
+    with _pool(threads) as ex:
+        v = list(ex.map(lambda j: comp_enc_unsigned(keys, *j), jobs))
+        vx = list(ex.map(lambda d: gate(keys, AND, v[4 * d], v[4 * d + 1]), range(D)))
+        vy = list(ex.map(lambda d: gate(keys, AND, v[4 * d + 2], v[4 * d + 3]), range(D)))
+        out = list(ex.map(lambda d: gate(keys, AND, vx[d], vy[d]), range(D)))
+    return np.stack(out) if D else np.zeros((0, keys.P.n + 1), np.uint32)
+
+
+def cov_enc_batch(keys: Keys, cell_cts, enc_cells, width: int, threads: int | None = None) -> np.ndarray:
+    """Alg. CoV with encrypted cells: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)),
+    both equality tests with bootstrapped XNORs (eq_enc).  cell_cts: [2w][n+1]
+    (x bits then y bits); enc_cells: [D][2w][n+1]."""
+    c = _u32(cell_cts)
+    E = _u32(enc_cells)
+    D = E.shape[0]
+    with _pool(threads) as ex:
+        vx = list(ex.map(lambda d: eq_enc(keys, c[:width], E[d, :width]), range(D)))
+        vy = list(ex.map(lambda d: eq_enc(keys, c[width:], E[d, width:]), range(D)))
+        out = list(ex.map(lambda d: gate(keys, AND, vx[d], vy[d]), range(D)))
+    return np.stack(out) if D else np.zeros((0, keys.P.n + 1), np.uint32)
+
+
+def idm_enc_batch(keys: Keys, x_cts, enc_ids, threads: int | None = None) -> np.ndarray:
+    """IdM match bits with encrypted ids (eq_enc per entry).  enc_ids: [D][l][n+1]."""
+    x = _u32(x_cts)
+    E = _u32(enc_ids)
+    with _pool(threads) as ex:
+        out = list(ex.map(lambda d: eq_enc(keys, x, E[d]), range(E.shape[0])))
+    return np.stack(out) if out else np.zeros((0, keys.P.n + 1), np.uint32)
+
+
+def idm_enc_payload(keys: Keys, x_cts, enc_ids, enc_payload, threads: int | None = None) -> np.ndarray:
+    """IdM with an encrypted payload: match bits, Alg. HomBitwiseAND (one
+    bootstrapped AND of the match bit with each payload bit), then the HomSum
+    XOR tree.  enc_payload: [D][lS][n+1]; returns [lS][n+1]."""
+    v = idm_enc_batch(keys, x_cts, enc_ids, threads)
+    Pay = _u32(enc_payload)
+    D, lS = Pay.shape[0], Pay.shape[1]
+    with _pool(threads) as ex:
+        flat = list(ex.map(lambda k: gate(keys, AND, v[k // lS], Pay[k // lS, k % lS]), range(D * lS)))
+    S = np.stack(flat).reshape(D, lS, -1)
     return homsum_tree(keys, S, threads)

@@ -440,6 +440,7 @@ struct ServeQuery {
     std::vector<uint32_t> db, payload;   // host copies of the plaintext database
     Program P;
     size_t cursor = 0;      // next layer
+    size_t offset = 0;      // gates of layer `cursor` already issued
     bool pre_done = false;
     size_t footprint = 0;
     uint32_t *dmem = nullptr;   // inputs + pool + output staging (one allocation)
@@ -502,6 +503,7 @@ int build_query(velopir_ctx *c, ServeQuery &s)
             build_cov(B, a.data(), q.db, q.D, out_base);
         else
             build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out_base);
+        if (c->path == VP_PATH_NTT) relayer(s.P, ntt_full_wave());
         allocate_slots(s.P);
         if (pass == 0) {
             s.footprint = (inw + (s.out_host ? s.out_words : 0) + (size_t)s.P.nphys * kSlotWords) * 4 + 256;
@@ -530,8 +532,12 @@ uint32_t *query_pool(const ServeQuery &s)
     return s.dmem + query_in_words(s.q) + (s.out_host ? s.out_words : 0);
 }
 
-// One serving step: every active query contributes its next layer; all of
-// them run as one merged launch sequence.
+// One serving step: the active queries contribute the gates of their current
+// layers, oldest query first, up to a whole number of full waves of the
+// blind-rotation kernel when at least one wave is available (else all of
+// them); all of them run as one merged launch sequence.  A query whose layer
+// is only partly issued continues it in the next step, so its layers still
+// run in order.
 int serve_step(velopir_ctx *c)
 {
     int rc;
@@ -553,9 +559,14 @@ int serve_step(velopir_ctx *c)
     size_t total_br = 0;
     for (auto &sp : c->active) {
         ServeQuery &s = *sp;
-        if (s.cursor < s.P.layers.size()) total_br += s.P.layers[s.cursor].br.size();
+        if (s.cursor < s.P.layers.size()) {
+            const Layer &L = s.P.layers[s.cursor];
+            total_br += L.br.size() - (s.offset < L.ks.size() ? (size_t)L.ks[s.offset].e0 : L.br.size());
+        }
     }
-    const int cap = (int)std::max<size_t>(2, std::min<size_t>(total_br, (size_t)c->big_rows));
+    const size_t wave = c->path == VP_PATH_NTT ? (size_t)ntt_full_wave() : 0;
+    const size_t take = (wave && total_br >= wave) ? total_br / wave * wave : total_br;
+    const int cap = (int)std::max<size_t>(2, std::min<size_t>(take, (size_t)c->big_rows));
     if ((rc = ensure(c, c->big, (size_t)cap * kBigWords * 4))) return rc;
     // Merge layer jobs of all queries into one virtual layer with rebased indices.
     Layer ML;
@@ -571,26 +582,34 @@ int serve_step(velopir_ctx *c)
             }
             s.pre_done = true;
         }
-        if (s.cursor >= s.P.layers.size()) continue;
+        if (s.cursor >= s.P.layers.size() || ML.br.size() >= take) continue;
         const Layer &L = s.P.layers[s.cursor];
-        const int base = (int)ML.br.size();
-        for (BrJob j : L.br) {
-            j.in0 = j.in0 ? resolve((uint64_t)(uintptr_t)j.in0, pool, s.P.phys) : nullptr;
-            j.in1 = j.in1 ? resolve((uint64_t)(uintptr_t)j.in1, pool, s.P.phys) : nullptr;
-            ML.br.push_back(j);
-        }
-        for (KsJob k : L.ks) {
-            k.e0 += base;
-            if (k.e1 >= 0) k.e1 += base;
+        // a gate's blind rotations are consecutive, in the order of its key switches
+        for (; s.offset < L.ks.size(); ++s.offset) {
+            KsJob k = L.ks[s.offset];
+            const size_t nbr = k.e1 >= 0 ? 2 : 1;
+            if (ML.br.size() + nbr > take && !ML.br.empty()) break;
+            const int base = (int)ML.br.size();
+            for (int e : {k.e0, k.e1}) {
+                if (e < 0) continue;
+                BrJob j = L.br[e];
+                j.in0 = j.in0 ? resolve((uint64_t)(uintptr_t)j.in0, pool, s.P.phys) : nullptr;
+                j.in1 = j.in1 ? resolve((uint64_t)(uintptr_t)j.in1, pool, s.P.phys) : nullptr;
+                ML.br.push_back(j);
+            }
+            k.e0 = base;
+            if (k.e1 >= 0) k.e1 = base + 1;
             k.out = resolve((uint64_t)(uintptr_t)k.out, pool, s.P.phys);
             ML.ks.push_back(k);
         }
+        if (s.offset < L.ks.size()) continue;   // the rest of this layer goes in the next step
         for (FreeJob f : L.fr) {
             f.in = f.in ? resolve((uint64_t)(uintptr_t)f.in, pool, s.P.phys) : nullptr;
             f.out = resolve((uint64_t)(uintptr_t)f.out, pool, s.P.phys);
             post.push_back(f);
         }
         s.cursor++;
+        s.offset = 0;
     }
     static const std::vector<int> nophys;
     flatten_free(pre, nullptr, nophys, merged);
@@ -943,6 +962,94 @@ int velopir_tuned_shape(velopir_ctx *c, size_t count)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
     return c->path == VP_PATH_NTT ? ntt_pick_warps((int)std::min<size_t>(count, 1u << 30)) : br_dense_jobs_per_cta();
+}
+
+// ---- encrypted database ----------------------------------------------------
+
+extern "C++" {
+namespace {
+
+// Stage the query and database ciphertexts (host or device) into the
+// context's input scratch, run the program `build` makes, write the outputs.
+template <typename F>
+int run_encdb(velopir_ctx *c, const uint32_t *q0, size_t q0_cts, const uint32_t *q1, size_t q1_cts,
+              const uint32_t *db0, size_t db0_cts, const uint32_t *db1, size_t db1_cts, uint32_t *out,
+              size_t out_cts, F build)
+{
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    cudaSetDevice(c->device);
+    int rc;
+    const size_t w[4] = {q0_cts * kLweWords, q1_cts * kLweWords, db0_cts * kLweWords, db1_cts * kLweWords};
+    if ((rc = ensure(c, c->in, std::max<size_t>(1, w[0] + w[1] + w[2] + w[3]) * 4))) return rc;
+    const uint32_t *src[4] = {q0, q1, db0, db1}, *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t at = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (src[i] && w[i] && (rc = stage_in(c, src[i], w[i], at, &dev[i]))) return rc;
+        at += w[i];
+    }
+    OutStage o;
+    if ((rc = stage_out(c, out, out_cts * kLweWords, o))) return rc;
+    Program P;
+    Builder B(P);
+    build(B, dev, o.dev);
+    if ((rc = run_program(c, P))) return rc;
+    return finish_out(c, o);
+}
+
+std::vector<Ref> inputs_of(Builder &B, const uint32_t *base, int count)
+{
+    std::vector<Ref> r(count);
+    for (int i = 0; i < count; ++i) r[i] = B.input(base + (size_t)i * kLweWords);
+    return r;
+}
+
+}  // namespace
+}  // extern "C++"
+
+int velopir_interval_query_encdb(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, int l,
+                                 const uint32_t *enc_rects, size_t D, uint32_t *out_bits)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (l < 1 || l > 32) return fail(c, VELOPIR_ERR_ARG, "l = %d is outside 1..32", l);
+    if (D == 0) return VELOPIR_OK;
+    if (!enc_x || !enc_y || !enc_rects || !out_bits) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    return run_encdb(c, enc_x, (size_t)l, enc_y, (size_t)l, enc_rects, D * 4 * (size_t)l, nullptr, 0, out_bits, D,
+                     [&](Builder &B, const uint32_t *const *dev, uint32_t *out) {
+                         const std::vector<Ref> x = inputs_of(B, dev[0], l), y = inputs_of(B, dev[1], l);
+                         build_intv_enc(B, x.data(), y.data(), l, dev[2], D, out);
+                     });
+}
+
+int velopir_coordinate_query_encdb(velopir_ctx *c, const uint32_t *enc_cell, int w, const uint32_t *enc_cells,
+                                   size_t D, uint32_t *out_bits)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (w < 1 || w > 16) return fail(c, VELOPIR_ERR_ARG, "w = %d is outside 1..16", w);
+    if (D == 0) return VELOPIR_OK;
+    if (!enc_cell || !enc_cells || !out_bits) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    return run_encdb(c, enc_cell, 2 * (size_t)w, nullptr, 0, enc_cells, D * 2 * (size_t)w, nullptr, 0, out_bits, D,
+                     [&](Builder &B, const uint32_t *const *dev, uint32_t *out) {
+                         const std::vector<Ref> cell = inputs_of(B, dev[0], 2 * w);
+                         build_cov_enc(B, cell.data(), w, dev[2], D, out);
+                     });
+}
+
+int velopir_id_match_encdb(velopir_ctx *c, const uint32_t *enc_id, int id_bits, const uint32_t *enc_ids, size_t D,
+                           const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (id_bits < 1 || id_bits > 32) return fail(c, VELOPIR_ERR_ARG, "id_bits = %d is outside 1..32", id_bits);
+    if (enc_payload && (payload_bits < 1 || payload_bits > 32))
+        return fail(c, VELOPIR_ERR_ARG, "payload_bits = %d is outside 1..32", payload_bits);
+    if (D == 0) return VELOPIR_OK;
+    if (!enc_id || !enc_ids || !out) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    const int pb = enc_payload ? payload_bits : 0;
+    return run_encdb(c, enc_id, (size_t)id_bits, nullptr, 0, enc_ids, D * (size_t)id_bits, enc_payload,
+                     D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
+                     [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
+                         const std::vector<Ref> id = inputs_of(B, dev[0], id_bits);
+                         build_idm_enc(B, id.data(), id_bits, dev[2], D, dev[3], pb, o);
+                     });
 }
 
 int velopir_interval_query(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, const uint32_t *rects,

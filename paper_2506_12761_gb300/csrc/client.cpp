@@ -104,6 +104,36 @@ int velopir_client_encrypt_bits(const uint32_t *s, const uint32_t *bits, const u
     return VELOPIR_OK;
 }
 
+int velopir_client_pubkeygen(const uint32_t *s, const uint32_t *a, const uint32_t *e, size_t count, uint32_t *pk_out)
+{
+    // Alg. PubKeyGen: one fresh encryption of zero per database bit, (a, <a, s> + e).
+    if (!s || !a || !e || (!pk_out && count)) return VELOPIR_ERR_ARG;
+    for (size_t c = 0; c < count; ++c) {
+        uint32_t dot = 0;
+        const uint32_t *ac = a + c * n;
+        uint32_t *o = pk_out + c * (n + 1);
+        for (int k = 0; k < n; ++k) {
+            o[k] = ac[k];
+            dot += (s[k] & 1u) ? ac[k] : 0u;
+        }
+        o[n] = dot + e[c];
+    }
+    return VELOPIR_OK;
+}
+
+int velopir_server_encrypt(const uint32_t *pk, const uint32_t *bits, size_t count, uint32_t *ct_out)
+{
+    // Alg. ServerEnc: ct = (0, Ecd(bit)) + pk, with Ecd(1) = 1/8 and Ecd(0) = -1/8.
+    if (!pk || !bits || (!ct_out && count)) return VELOPIR_ERR_ARG;
+    for (size_t c = 0; c < count; ++c) {
+        const uint32_t *p = pk + c * (n + 1);
+        uint32_t *o = ct_out + c * (n + 1);
+        for (int k = 0; k < n; ++k) o[k] = p[k];
+        o[n] = p[n] + (bits[c] ? MU : 0u - MU);
+    }
+    return VELOPIR_OK;
+}
+
 int velopir_client_decrypt_bits(const uint32_t *s, const uint32_t *ct, size_t count, uint32_t *bits_out)
 {
     if (!s || !ct || (!bits_out && count)) return VELOPIR_ERR_ARG;

@@ -221,6 +221,103 @@ void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size
         for (int j = 0; j < payload_bits; ++j) B.materialize(S[j], out + (size_t)j * kLweWords);
 }
 
+Ref build_compare_enc(Builder &B, const Ref *c1, const Ref *c2, int l, bool strict, bool is_unsigned)
+{
+    // Alg. HomCompLeOPT (HomCompL for strict) with both operands encrypted:
+    // t0 = XOR of the top bits; t1 = T(+-1/8); t1 = MUX(XNOR(c1_i, c2_i), t1, c2_i)
+    // for i = 0..l-2 (the XNORs are independent, the MUXes ripple); the result
+    // is MUX(t0, c1_top, t1).  Signed two's complement as in the paper; the
+    // unsigned form flips both top bits first (free NOTs).
+    Ref top1 = c1[l - 1], top2 = c2[l - 1];
+    if (is_unsigned) {
+        top1 = Builder::neg(top1);
+        top2 = Builder::neg(top2);
+    }
+    const Ref t0 = B.gate(G_XOR, top1, top2);
+    std::vector<Ref> tx(l > 1 ? l - 1 : 0);
+    for (int i = 0; i + 1 < l; ++i) tx[i] = B.gate(G_XNOR, c1[i], c2[i]);
+    Ref t1 = Builder::trivial(strict ? 0u - kMu : kMu);
+    for (int i = 0; i + 1 < l; ++i) t1 = B.mux(tx[i], t1, c2[i]);
+    return B.mux(t0, top1, t1);
+}
+
+Ref build_eq_enc(Builder &B, const Ref *x, const Ref *y, int l, uint32_t *out)
+{
+    // Alg. HomEqOPT with both operands encrypted: bootstrapped XNORs, then the
+    // pairwise AND reduction t[i] = AND(t[i], t[i+k]) for k = 1, 2, 4, ...
+    std::vector<Ref> t(l);
+    for (int i = 0; i < l; ++i) t[i] = B.gate(G_XNOR, x[i], y[i], (out && l == 1) ? out : nullptr);
+    int last_k = 0;
+    for (int k = 1; k < l; k *= 2) last_k = k;
+    for (int k = 1; k < l; k *= 2)
+        for (int i = 0; i + k < l; i += 2 * k)
+            t[i] = B.gate(G_AND, t[i], t[i + k], (out && k == last_k && i == 0) ? out : nullptr);
+    return t[0];
+}
+
+static std::vector<Ref> enc_inputs(Builder &B, const uint32_t *base, int count)
+{
+    std::vector<Ref> r(count);
+    for (int i = 0; i < count; ++i) r[i] = B.input(base + (size_t)i * kLweWords);
+    return r;
+}
+
+void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D, uint32_t *out)
+{
+    // Alg. InterValid with encrypted bounds: AND(AND(LE(x_lo,x), L(x,x_hi)), AND(LE(y_lo,y), L(y,y_hi))).
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> r = enc_inputs(B, enc_rects + d * 4 * (size_t)l * kLweWords, 4 * l);
+        Ref vxl = build_compare_enc(B, r.data(), x, l, false, true);
+        Ref vxr = build_compare_enc(B, x, r.data() + l, l, true, true);
+        Ref vyl = build_compare_enc(B, r.data() + 2 * l, y, l, false, true);
+        Ref vyr = build_compare_enc(B, y, r.data() + 3 * l, l, true, true);
+        Ref vx = B.gate(G_AND, vxl, vxr);
+        Ref vy = B.gate(G_AND, vyl, vyr);
+        B.gate(G_AND, vx, vy, out + d * kLweWords);
+    }
+}
+
+void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D, uint32_t *out)
+{
+    // Alg. CoV with encrypted cells: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)).
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> c = enc_inputs(B, enc_cells + d * 2 * (size_t)w * kLweWords, 2 * w);
+        Ref vx = build_eq_enc(B, cell, c.data(), w);
+        Ref vy = build_eq_enc(B, cell + w, c.data() + w, w);
+        B.gate(G_AND, vx, vy, out + d * kLweWords);
+    }
+}
+
+void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+{
+    if (!enc_payload) {
+        for (size_t d = 0; d < D; ++d) {
+            const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
+            build_eq_enc(B, id, c.data(), id_bits, out + d * kLweWords);
+        }
+        return;
+    }
+    // Match bits, Alg. HomBitwiseAND with an encrypted payload (one bootstrapped
+    // AND per payload bit), then the pairwise HomSum XOR reduction per bit.
+    std::vector<Ref> S(D * (size_t)payload_bits);
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
+        const Ref v = build_eq_enc(B, id, c.data(), id_bits);
+        const std::vector<Ref> pay = enc_inputs(B, enc_payload + d * (size_t)payload_bits * kLweWords, payload_bits);
+        for (int j = 0; j < payload_bits; ++j)
+            S[d * payload_bits + j] = B.gate(G_AND, v, pay[j], (D == 1) ? out + (size_t)j * kLweWords : nullptr);
+    }
+    size_t last_k = 0;
+    for (size_t k = 1; k < D; k *= 2) last_k = k;
+    for (size_t k = 1; k < D; k *= 2)
+        for (size_t i = 0; i + k < D; i += 2 * k)
+            for (int j = 0; j < payload_bits; ++j) {
+                uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
+            }
+}
+
 void relayer(Program &p, int wave)
 {
     if (wave <= 0 || p.layers.size() <= 1) return;

@@ -77,6 +77,21 @@ void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uin
 void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
                int payload_bits, uint32_t *out);
 
+// Circuits with an encrypted database (the paper's protocol: Alg. ServerEnc
+// encrypts every database bit).  Database operands are ciphertexts (device
+// pointers, 631 words each, bits LSB first), so the XNORs of the equality
+// tests and the XNOR/MUX ripple of the comparators are bootstrapped.
+// c1 <= c2 (strict: c1 < c2), l-bit, unsigned through the top-bit flip.
+Ref build_compare_enc(Builder &B, const Ref *c1, const Ref *c2, int l, bool strict, bool is_unsigned);
+Ref build_eq_enc(Builder &B, const Ref *x, const Ref *y, int l, uint32_t *out = nullptr);
+// enc_rects: [D][4][l] ciphertexts (x_lo, x_hi, y_lo, y_hi).
+void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D, uint32_t *out);
+// cell: 2w ciphertexts (x then y); enc_cells: [D][2w].
+void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D, uint32_t *out);
+// enc_ids: [D][id_bits]; enc_payload: [D][payload_bits] or null.
+void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+
 // Wave-filling list schedule (replaces the as-soon-as-possible layers of a
 // built program, before allocate_slots).  A gate may run in any launch after
 // the launches of the gates it reads; each launch takes, among the ready

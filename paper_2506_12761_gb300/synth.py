@@ -37,6 +37,7 @@ STREAM_KEYS = 1
 STREAM_QUERY = 2
 STREAM_DB = 3
 STREAM_ARRIVALS = 4
+STREAM_PUBKEY = 5   # Alg. PubKeyGen material (masks and noises of the encryptions of zero)
 
 _SIGMA = np.uint32(0x61707865), np.uint32(0x3320646E), np.uint32(0x79622D32), np.uint32(0x6B206574)
 

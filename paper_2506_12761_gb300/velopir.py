@@ -35,7 +35,8 @@ EXPORTS = [
     "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
-    "velopir_selftest_wait_timeout", "velopir_plan_query",
+    "velopir_selftest_wait_timeout", "velopir_plan_query", "velopir_client_pubkeygen", "velopir_server_encrypt",
+    "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb",
 ]
 NOALLOC_MAX_GATES = 256
 NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
@@ -101,6 +102,11 @@ def lib() -> ctypes.CDLL:
             "velopir_autotune": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
             "velopir_tuned_shape": (i, [vp, sz]),
             "velopir_plan_query": (i, [ctypes.POINTER(Query), i, vp, vp, vp, ctypes.POINTER(sz), i]),
+            "velopir_client_pubkeygen": (i, [vp, vp, vp, sz, vp]),
+            "velopir_server_encrypt": (i, [vp, vp, sz, vp]),
+            "velopir_interval_query_encdb": (i, [vp, vp, vp, i, vp, sz, vp]),
+            "velopir_coordinate_query_encdb": (i, [vp, vp, i, vp, sz, vp]),
+            "velopir_id_match_encdb": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(ctypes.c_double)]),
         }
@@ -335,3 +341,37 @@ def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0
     if rc < 0:
         raise VelopirError(rc, "velopir_plan_query")
     return out[:nout], [int(sizes[k]) for k in range(min(rc, max_launches))]
+
+
+def velopir_client_pubkeygen(s, lwe_mat_zero) -> np.ndarray:
+    """Alg. PubKeyGen: encryptions of zero from (a, e) material (synth.lwe_material)."""
+    s = np.ascontiguousarray(s, dtype=np.uint32)
+    a = np.ascontiguousarray(lwe_mat_zero.a, dtype=np.uint32)
+    e = np.ascontiguousarray(lwe_mat_zero.e, dtype=np.uint32)
+    count = e.shape[0]
+    out = np.zeros((count, LWE_WORDS), dtype=np.uint32)
+    _check(None, lib().velopir_client_pubkeygen(ptr(s), ptr(a), ptr(e), count, ptr(out)))
+    return out
+
+
+def velopir_server_encrypt(pk, bits) -> np.ndarray:
+    """Alg. ServerEnc: (0, Ecd(bit)) + pk, one ciphertext per bit (any leading shape)."""
+    pk = np.ascontiguousarray(pk, dtype=np.uint32).reshape(-1, LWE_WORDS)
+    b = np.ascontiguousarray(bits, dtype=np.uint32).reshape(-1)
+    assert pk.shape[0] == b.shape[0]
+    out = np.zeros_like(pk)
+    _check(None, lib().velopir_server_encrypt(ptr(pk), ptr(b), b.shape[0], ptr(out)))
+    return out.reshape(np.shape(bits) + (LWE_WORDS,))
+
+
+def velopir_interval_query_encdb(ctx, enc_x, enc_y, l: int, enc_rects, D: int, out_bits) -> None:
+    _check(ctx, lib().velopir_interval_query_encdb(ctx, ptr(enc_x), ptr(enc_y), l, ptr(enc_rects), D, ptr(out_bits)))
+
+
+def velopir_coordinate_query_encdb(ctx, enc_cell, w: int, enc_cells, D: int, out_bits) -> None:
+    _check(ctx, lib().velopir_coordinate_query_encdb(ctx, ptr(enc_cell), w, ptr(enc_cells), D, ptr(out_bits)))
+
+
+def velopir_id_match_encdb(ctx, enc_id, id_bits: int, enc_ids, D: int, enc_payload, payload_bits: int, out) -> None:
+    _check(ctx, lib().velopir_id_match_encdb(ctx, ptr(enc_id), id_bits, ptr(enc_ids), D, ptr(enc_payload),
+                                             payload_bits, ptr(out)))
