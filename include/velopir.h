@@ -213,30 +213,37 @@ int velopir_client_pubkeygen(const uint32_t *s, const uint32_t *a, const uint32_
  * uint32_t[count][631].  Host only; uses no secret.  Errors: ERR_ARG. */
 int velopir_server_encrypt(const uint32_t *pk, const uint32_t *bits, size_t count, uint32_t *ct_out);
 
-/* IntV over an encrypted database (Alg. InterValid): out_bits[d] =
- * Enc(x_lo <= x < x_hi && y_lo <= y < y_hi) for l-bit unsigned coordinates
+/* Largest encrypted payload (bits per entry) of the encdb calls. */
+#define VELOPIR_MAX_ENC_PAYLOAD_BITS 4096
+
+/* Every encdb call has the same payload convention.  enc_payload == NULL:
+ * out = [D][631], one validation bit per entry.  Otherwise enc_payload =
+ * [D][payload_bits][631] (1 <= payload_bits <= VELOPIR_MAX_ENC_PAYLOAD_BITS,
+ * the paper's l_S), each entry's payload is zeroed by its validation bit with
+ * one bootstrapped AND per bit (Alg. HomBitwiseAND) and the D results are
+ * XOR-aggregated pairwise (Section 5's HomSum, (D-1) payload_bits bootstraps):
+ * out = [payload_bits][631], the XOR of the payloads of the valid entries. */
+
+/* IntV over an encrypted database (Alg. InterValid): validation bit
+ * (x_lo <= x < x_hi && y_lo <= y < y_hi) for l-bit unsigned coordinates
  * (1 <= l <= 32; the paper's interval precision l_I).  enc_x, enc_y:
  * [l][631]; enc_rects: [D][4][l][631] (x_lo, x_hi, y_lo, y_hi, bits LSB
- * first); out_bits: [D][631].  12 l + 3 bootstraps per entry (per
- * comparator: 1 XOR, l-1 XNORs, l MUXes of 2).  Errors: ERR_ARG, ERR_NOKEY,
- * ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
+ * first).  12 l + 3 bootstraps per entry (per comparator: 1 XOR, l-1 XNORs,
+ * l MUXes of 2).  Errors: ERR_ARG, ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
 int velopir_interval_query_encdb(velopir_ctx *ctx, const uint32_t *enc_x, const uint32_t *enc_y, int l,
-                                 const uint32_t *enc_rects, size_t D, uint32_t *out_bits);
+                                 const uint32_t *enc_rects, size_t D, const uint32_t *enc_payload,
+                                 int payload_bits, uint32_t *out);
 
-/* CoV over an encrypted database (Alg. CoV with Alg. HomEqOPT): enc_cell:
- * [2w][631] (w bits of x, then w bits of y; 1 <= w <= 16), enc_cells:
- * [D][2w][631]; out_bits[d] = Enc(cell == cell_d): [D][631].  4 w - 1
- * bootstraps per entry.  Errors: as above. */
-int velopir_coordinate_query_encdb(velopir_ctx *ctx, const uint32_t *enc_cell, int w, const uint32_t *enc_cells,
-                                   size_t D, uint32_t *out_bits);
-
-/* IdM over an encrypted database: enc_id: [id_bits][631] (1..32 bits),
- * enc_ids: [D][id_bits][631].  enc_payload == NULL: out = [D][631] match
- * bits (2 id_bits - 1 bootstraps per entry).  Otherwise enc_payload:
- * [D][payload_bits][631] (1..32 bits), each zeroed by its entry's match bit
- * with a bootstrapped AND and XOR-aggregated (Section 5's HomSum): out =
- * [payload_bits][631], the payload of the matching entry (0 if none).
+/* CoV over an encrypted database (Alg. CoV with Alg. HomEqOPT): validation
+ * bit (cell == cell_d).  enc_cell: [2w][631] (w bits of x, then w bits of y;
+ * 1 <= w <= 16), enc_cells: [D][2w][631].  4 w - 1 bootstraps per entry.
  * Errors: as above. */
+int velopir_coordinate_query_encdb(velopir_ctx *ctx, const uint32_t *enc_cell, int w, const uint32_t *enc_cells,
+                                   size_t D, const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+
+/* IdM over an encrypted database: validation bit (id == id_d).  enc_id:
+ * [id_bits][631] (1..32 bits), enc_ids: [D][id_bits][631].  2 id_bits - 1
+ * bootstraps per entry.  Errors: as above. */
 int velopir_id_match_encdb(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, const uint32_t *enc_ids,
                            size_t D, const uint32_t *enc_payload, int payload_bits, uint32_t *out);
 

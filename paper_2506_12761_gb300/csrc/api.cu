@@ -969,6 +969,8 @@ int velopir_tuned_shape(velopir_ctx *c, size_t count)
 extern "C++" {
 namespace {
 
+constexpr int kMaxEncPayloadBits = 4096;   // VELOPIR_MAX_ENC_PAYLOAD_BITS
+
 // Stage the query and database ciphertexts (host or device) into the
 // context's input scratch, run the program `build` makes, write the outputs.
 template <typename F>
@@ -1007,30 +1009,39 @@ std::vector<Ref> inputs_of(Builder &B, const uint32_t *base, int count)
 }  // extern "C++"
 
 int velopir_interval_query_encdb(velopir_ctx *c, const uint32_t *enc_x, const uint32_t *enc_y, int l,
-                                 const uint32_t *enc_rects, size_t D, uint32_t *out_bits)
+                                 const uint32_t *enc_rects, size_t D, const uint32_t *enc_payload, int payload_bits,
+                                 uint32_t *out)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
     if (l < 1 || l > 32) return fail(c, VELOPIR_ERR_ARG, "l = %d is outside 1..32", l);
+    if (enc_payload && (payload_bits < 1 || payload_bits > kMaxEncPayloadBits))
+        return fail(c, VELOPIR_ERR_ARG, "payload_bits = %d is outside 1..%d", payload_bits, kMaxEncPayloadBits);
     if (D == 0) return VELOPIR_OK;
-    if (!enc_x || !enc_y || !enc_rects || !out_bits) return fail(c, VELOPIR_ERR_ARG, "null argument");
-    return run_encdb(c, enc_x, (size_t)l, enc_y, (size_t)l, enc_rects, D * 4 * (size_t)l, nullptr, 0, out_bits, D,
-                     [&](Builder &B, const uint32_t *const *dev, uint32_t *out) {
+    if (!enc_x || !enc_y || !enc_rects || !out) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    const int pb = enc_payload ? payload_bits : 0;
+    return run_encdb(c, enc_x, (size_t)l, enc_y, (size_t)l, enc_rects, D * 4 * (size_t)l, enc_payload,
+                     D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
+                     [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
                          const std::vector<Ref> x = inputs_of(B, dev[0], l), y = inputs_of(B, dev[1], l);
-                         build_intv_enc(B, x.data(), y.data(), l, dev[2], D, out);
+                         build_intv_enc(B, x.data(), y.data(), l, dev[2], D, dev[3], pb, o);
                      });
 }
 
 int velopir_coordinate_query_encdb(velopir_ctx *c, const uint32_t *enc_cell, int w, const uint32_t *enc_cells,
-                                   size_t D, uint32_t *out_bits)
+                                   size_t D, const uint32_t *enc_payload, int payload_bits, uint32_t *out)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
     if (w < 1 || w > 16) return fail(c, VELOPIR_ERR_ARG, "w = %d is outside 1..16", w);
+    if (enc_payload && (payload_bits < 1 || payload_bits > kMaxEncPayloadBits))
+        return fail(c, VELOPIR_ERR_ARG, "payload_bits = %d is outside 1..%d", payload_bits, kMaxEncPayloadBits);
     if (D == 0) return VELOPIR_OK;
-    if (!enc_cell || !enc_cells || !out_bits) return fail(c, VELOPIR_ERR_ARG, "null argument");
-    return run_encdb(c, enc_cell, 2 * (size_t)w, nullptr, 0, enc_cells, D * 2 * (size_t)w, nullptr, 0, out_bits, D,
-                     [&](Builder &B, const uint32_t *const *dev, uint32_t *out) {
+    if (!enc_cell || !enc_cells || !out) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    const int pb = enc_payload ? payload_bits : 0;
+    return run_encdb(c, enc_cell, 2 * (size_t)w, nullptr, 0, enc_cells, D * 2 * (size_t)w, enc_payload,
+                     D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
+                     [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
                          const std::vector<Ref> cell = inputs_of(B, dev[0], 2 * w);
-                         build_cov_enc(B, cell.data(), w, dev[2], D, out);
+                         build_cov_enc(B, cell.data(), w, dev[2], D, dev[3], pb, o);
                      });
 }
 
@@ -1039,8 +1050,8 @@ int velopir_id_match_encdb(velopir_ctx *c, const uint32_t *enc_id, int id_bits, 
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
     if (id_bits < 1 || id_bits > 32) return fail(c, VELOPIR_ERR_ARG, "id_bits = %d is outside 1..32", id_bits);
-    if (enc_payload && (payload_bits < 1 || payload_bits > 32))
-        return fail(c, VELOPIR_ERR_ARG, "payload_bits = %d is outside 1..32", payload_bits);
+    if (enc_payload && (payload_bits < 1 || payload_bits > kMaxEncPayloadBits))
+        return fail(c, VELOPIR_ERR_ARG, "payload_bits = %d is outside 1..%d", payload_bits, kMaxEncPayloadBits);
     if (D == 0) return VELOPIR_OK;
     if (!enc_id || !enc_ids || !out) return fail(c, VELOPIR_ERR_ARG, "null argument");
     const int pb = enc_payload ? payload_bits : 0;

@@ -262,51 +262,18 @@ static std::vector<Ref> enc_inputs(Builder &B, const uint32_t *base, int count)
     return r;
 }
 
-void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D, uint32_t *out)
+// Alg. HomBitwiseAND with encrypted payloads (one bootstrapped AND of the
+// validation bit with each payload bit), then the pairwise HomSum XOR
+// reduction of Section 5 per payload bit into out.
+static void aggregate_enc(Builder &B, const std::vector<Ref> &v, const uint32_t *enc_payload, int payload_bits,
+                          uint32_t *out)
 {
-    // Alg. InterValid with encrypted bounds: AND(AND(LE(x_lo,x), L(x,x_hi)), AND(LE(y_lo,y), L(y,y_hi))).
-    for (size_t d = 0; d < D; ++d) {
-        const std::vector<Ref> r = enc_inputs(B, enc_rects + d * 4 * (size_t)l * kLweWords, 4 * l);
-        Ref vxl = build_compare_enc(B, r.data(), x, l, false, true);
-        Ref vxr = build_compare_enc(B, x, r.data() + l, l, true, true);
-        Ref vyl = build_compare_enc(B, r.data() + 2 * l, y, l, false, true);
-        Ref vyr = build_compare_enc(B, y, r.data() + 3 * l, l, true, true);
-        Ref vx = B.gate(G_AND, vxl, vxr);
-        Ref vy = B.gate(G_AND, vyl, vyr);
-        B.gate(G_AND, vx, vy, out + d * kLweWords);
-    }
-}
-
-void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D, uint32_t *out)
-{
-    // Alg. CoV with encrypted cells: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)).
-    for (size_t d = 0; d < D; ++d) {
-        const std::vector<Ref> c = enc_inputs(B, enc_cells + d * 2 * (size_t)w * kLweWords, 2 * w);
-        Ref vx = build_eq_enc(B, cell, c.data(), w);
-        Ref vy = build_eq_enc(B, cell + w, c.data() + w, w);
-        B.gate(G_AND, vx, vy, out + d * kLweWords);
-    }
-}
-
-void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
-                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
-{
-    if (!enc_payload) {
-        for (size_t d = 0; d < D; ++d) {
-            const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
-            build_eq_enc(B, id, c.data(), id_bits, out + d * kLweWords);
-        }
-        return;
-    }
-    // Match bits, Alg. HomBitwiseAND with an encrypted payload (one bootstrapped
-    // AND per payload bit), then the pairwise HomSum XOR reduction per bit.
+    const size_t D = v.size();
     std::vector<Ref> S(D * (size_t)payload_bits);
     for (size_t d = 0; d < D; ++d) {
-        const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
-        const Ref v = build_eq_enc(B, id, c.data(), id_bits);
         const std::vector<Ref> pay = enc_inputs(B, enc_payload + d * (size_t)payload_bits * kLweWords, payload_bits);
         for (int j = 0; j < payload_bits; ++j)
-            S[d * payload_bits + j] = B.gate(G_AND, v, pay[j], (D == 1) ? out + (size_t)j * kLweWords : nullptr);
+            S[d * payload_bits + j] = B.gate(G_AND, v[d], pay[j], (D == 1) ? out + (size_t)j * kLweWords : nullptr);
     }
     size_t last_k = 0;
     for (size_t k = 1; k < D; k *= 2) last_k = k;
@@ -316,6 +283,49 @@ void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_i
                 uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
                 S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
             }
+}
+
+void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D,
+                    const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+{
+    // Alg. InterValid with encrypted bounds: AND(AND(LE(x_lo,x), L(x,x_hi)), AND(LE(y_lo,y), L(y,y_hi))).
+    std::vector<Ref> v(D);
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> r = enc_inputs(B, enc_rects + d * 4 * (size_t)l * kLweWords, 4 * l);
+        Ref vxl = build_compare_enc(B, r.data(), x, l, false, true);
+        Ref vxr = build_compare_enc(B, x, r.data() + l, l, true, true);
+        Ref vyl = build_compare_enc(B, r.data() + 2 * l, y, l, false, true);
+        Ref vyr = build_compare_enc(B, y, r.data() + 3 * l, l, true, true);
+        Ref vx = B.gate(G_AND, vxl, vxr);
+        Ref vy = B.gate(G_AND, vyl, vyr);
+        v[d] = B.gate(G_AND, vx, vy, enc_payload ? nullptr : out + d * kLweWords);
+    }
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
+}
+
+void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D,
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+{
+    // Alg. CoV with encrypted cells: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)).
+    std::vector<Ref> v(D);
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> c = enc_inputs(B, enc_cells + d * 2 * (size_t)w * kLweWords, 2 * w);
+        Ref vx = build_eq_enc(B, cell, c.data(), w);
+        Ref vy = build_eq_enc(B, cell + w, c.data() + w, w);
+        v[d] = B.gate(G_AND, vx, vy, enc_payload ? nullptr : out + d * kLweWords);
+    }
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
+}
+
+void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+{
+    std::vector<Ref> v(D);
+    for (size_t d = 0; d < D; ++d) {
+        const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
+        v[d] = build_eq_enc(B, id, c.data(), id_bits, enc_payload ? nullptr : out + d * kLweWords);
+    }
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
 }
 
 void relayer(Program &p, int wave)

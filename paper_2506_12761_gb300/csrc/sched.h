@@ -84,11 +84,16 @@ void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size
 // c1 <= c2 (strict: c1 < c2), l-bit, unsigned through the top-bit flip.
 Ref build_compare_enc(Builder &B, const Ref *c1, const Ref *c2, int l, bool strict, bool is_unsigned);
 Ref build_eq_enc(Builder &B, const Ref *x, const Ref *y, int l, uint32_t *out = nullptr);
-// enc_rects: [D][4][l] ciphertexts (x_lo, x_hi, y_lo, y_hi).
-void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D, uint32_t *out);
+// enc_rects: [D][4][l] ciphertexts (x_lo, x_hi, y_lo, y_hi).  With
+// enc_payload ([D][payload_bits] ciphertexts) each entry's payload is zeroed
+// by its validation bit and the results are XOR-aggregated into out
+// ([payload_bits] ciphertexts); without it out receives the D bits.
+void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D,
+                    const uint32_t *enc_payload, int payload_bits, uint32_t *out);
 // cell: 2w ciphertexts (x then y); enc_cells: [D][2w].
-void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D, uint32_t *out);
-// enc_ids: [D][id_bits]; enc_payload: [D][payload_bits] or null.
+void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D,
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+// enc_ids: [D][id_bits].
 void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
                    const uint32_t *enc_payload, int payload_bits, uint32_t *out);
 

@@ -104,8 +104,8 @@ def lib() -> ctypes.CDLL:
             "velopir_plan_query": (i, [ctypes.POINTER(Query), i, vp, vp, vp, ctypes.POINTER(sz), i]),
             "velopir_client_pubkeygen": (i, [vp, vp, vp, sz, vp]),
             "velopir_server_encrypt": (i, [vp, vp, sz, vp]),
-            "velopir_interval_query_encdb": (i, [vp, vp, vp, i, vp, sz, vp]),
-            "velopir_coordinate_query_encdb": (i, [vp, vp, i, vp, sz, vp]),
+            "velopir_interval_query_encdb": (i, [vp, vp, vp, i, vp, sz, vp, i, vp]),
+            "velopir_coordinate_query_encdb": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_id_match_encdb": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(ctypes.c_double)]),
@@ -364,12 +364,16 @@ def velopir_server_encrypt(pk, bits) -> np.ndarray:
     return out.reshape(np.shape(bits) + (LWE_WORDS,))
 
 
-def velopir_interval_query_encdb(ctx, enc_x, enc_y, l: int, enc_rects, D: int, out_bits) -> None:
-    _check(ctx, lib().velopir_interval_query_encdb(ctx, ptr(enc_x), ptr(enc_y), l, ptr(enc_rects), D, ptr(out_bits)))
+def velopir_interval_query_encdb(ctx, enc_x, enc_y, l: int, enc_rects, D: int, enc_payload, payload_bits: int,
+                                 out) -> None:
+    _check(ctx, lib().velopir_interval_query_encdb(ctx, ptr(enc_x), ptr(enc_y), l, ptr(enc_rects), D,
+                                                   ptr(enc_payload), payload_bits, ptr(out)))
 
 
-def velopir_coordinate_query_encdb(ctx, enc_cell, w: int, enc_cells, D: int, out_bits) -> None:
-    _check(ctx, lib().velopir_coordinate_query_encdb(ctx, ptr(enc_cell), w, ptr(enc_cells), D, ptr(out_bits)))
+def velopir_coordinate_query_encdb(ctx, enc_cell, w: int, enc_cells, D: int, enc_payload, payload_bits: int,
+                                   out) -> None:
+    _check(ctx, lib().velopir_coordinate_query_encdb(ctx, ptr(enc_cell), w, ptr(enc_cells), D, ptr(enc_payload),
+                                                     payload_bits, ptr(out)))
 
 
 def velopir_id_match_encdb(ctx, enc_id, id_bits: int, enc_ids, D: int, enc_payload, payload_bits: int, out) -> None:

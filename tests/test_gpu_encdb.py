@@ -29,9 +29,16 @@ def test_intv_encdb_matches_oracle(paper_keys):
     cx, cy = encrypt_value_bits(s, x, l, 900), encrypt_value_bits(s, y, l, 901)
     enc = server_enc(s, rects.reshape(-1), l, 902).reshape(3, 4, l, 631)
     out = np.zeros((3, 631), dtype=np.uint32)
-    vp.velopir_interval_query_encdb(ctx.h, cx, cy, l, enc, 3, out)
-    assert np.array_equal(out, oracle.intv_enc_batch(paper_keys, cx, cy, enc))
+    vp.velopir_interval_query_encdb(ctx.h, cx, cy, l, enc, 3, None, 0, out)
+    v = oracle.intv_enc_batch(paper_keys, cx, cy, enc)
+    assert np.array_equal(out, v)
     assert list(vp.velopir_client_decrypt_bits(s, out)) == [1, 0, 1]
+    # with 2-bit payloads: the XOR of the payloads of entries 0 and 2
+    P = server_enc(s, [1, 2, 3], 2, 903)
+    agg = np.zeros((2, 631), dtype=np.uint32)
+    vp.velopir_interval_query_encdb(ctx.h, cx, cy, l, enc, 3, P, 2, agg)
+    assert np.array_equal(agg, oracle.aggregate_enc(paper_keys, v, P))
+    assert list(vp.velopir_client_decrypt_bits(s, agg)) == [0, 1]
 
 
 def test_cov_encdb_matches_oracle(paper_keys):
@@ -42,7 +49,7 @@ def test_cov_encdb_matches_oracle(paper_keys):
     cq = encrypt_value_bits(s, q, 2 * w, 910)
     enc = server_enc(s, cells, 2 * w, 911)
     out = np.zeros((4, 631), dtype=np.uint32)
-    vp.velopir_coordinate_query_encdb(ctx.h, cq, w, enc, 4, out)
+    vp.velopir_coordinate_query_encdb(ctx.h, cq, w, enc, 4, None, 0, out)
     assert np.array_equal(out, oracle.cov_enc_batch(paper_keys, cq, enc, w))
     assert list(vp.velopir_client_decrypt_bits(s, out)) == [1, 0, 0, 0]
 
@@ -82,7 +89,7 @@ def test_intv_encdb_paper_precision_device_buffers(paper_keys):
     dout = torch.zeros((D, 631), dtype=torch.int32, device="cuda")
     vp.velopir_interval_query_encdb(ctx.h, torch.from_numpy(cx.view(np.int32)).cuda(),
                                     torch.from_numpy(cy.view(np.int32)).cuda(), l,
-                                    torch.from_numpy(enc.view(np.int32)).cuda(), D, dout)
+                                    torch.from_numpy(enc.view(np.int32)).cuda(), D, None, 0, dout)
     out = dout.cpu().numpy().view(np.uint32)
     r = rects.astype(np.int64)
     want = ((r[:, 0] <= x) & (x < r[:, 1]) & (r[:, 2] <= y) & (y < r[:, 3])).astype(np.uint32)
@@ -94,9 +101,11 @@ def test_encdb_bad_arguments():
     ctx, s = gpu_ctx()
     z = np.zeros((4, 631), dtype=np.uint32)
     with pytest.raises(vp.VelopirError):
-        vp.velopir_interval_query_encdb(ctx.h, z, z, 0, z, 1, z)
+        vp.velopir_interval_query_encdb(ctx.h, z, z, 0, z, 1, None, 0, z)
     with pytest.raises(vp.VelopirError):
-        vp.velopir_coordinate_query_encdb(ctx.h, z, 17, z, 1, z)
+        vp.velopir_coordinate_query_encdb(ctx.h, z, 17, z, 1, None, 0, z)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_coordinate_query_encdb(ctx.h, z, 4, z, 1, z, 4097, z)
     with pytest.raises(vp.VelopirError):
         vp.velopir_id_match_encdb(ctx.h, z, 33, z, 1, None, 0, z)
     vp.velopir_id_match_encdb(ctx.h, z, 4, z, 0, None, 0, z)   # D = 0 is a no-op

@@ -108,3 +108,20 @@ def test_toy_idm_enc_payload(toy_keys):
     assert list(oracle.decrypt_bits(toy_keys.s, agg)) == bits_of(pay[ids.index(q)], lS)
     miss = oracle.idm_enc_payload(toy_keys, enc_value(toy_keys, 1, l, 701), E, P)
     assert list(oracle.decrypt_bits(toy_keys.s, miss)) == [0] * lS
+
+
+def test_toy_aggregate_xors_the_valid_payloads(toy_keys):
+    """With several valid entries the aggregate is the XOR of their payloads
+    (HomSum of the zeroed payloads), including a single entry (no XOR)."""
+    lS = 4
+    valid = [1, 0, 1, 1, 0, 1, 0]
+    pay = [9, 3, 5, 12, 15, 6, 1]
+    v = np.stack([server_enc_value(toy_keys, b, 1, 1000 + d)[0] for d, b in enumerate(valid)])
+    P = np.stack([server_enc_value(toy_keys, p, lS, 1100 + d) for d, p in enumerate(pay)])
+    agg = oracle.aggregate_enc(toy_keys, v, P)
+    want = 0
+    for b, p in zip(valid, pay):
+        want ^= p if b else 0
+    assert list(oracle.decrypt_bits(toy_keys.s, agg)) == bits_of(want, lS)
+    one = oracle.aggregate_enc(toy_keys, v[:1], P[:1])
+    assert list(oracle.decrypt_bits(toy_keys.s, one)) == bits_of(pay[0], lS)
