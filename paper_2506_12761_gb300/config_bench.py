@@ -79,7 +79,7 @@ def run_idm32(ctx, s):
 
 def run_cov64(ctx, s):
     sizes = synth.log_uniform_sizes(64, 256, 16384, substream=9)
-    recs, checks = [], []
+    recs, checks, keep = [], [], []   # the records hold raw pointers: keep every buffer alive
     for q, D in enumerate(sizes):
         w = synth.cov_workload(int(D), substream=100 + q)
         cell = vp.velopir_client_encrypt_bits(s, synth.value_bits([w["cell"]], 32)[0],
@@ -87,6 +87,7 @@ def run_cov64(ctx, s):
         cells = w["cells"].astype(np.uint32)
         out = np.zeros((int(D), 631), dtype=np.uint32)
         recs.append(vp.make_query(vp.VP_QUERY_COV, cell, cells, int(D), out))
+        keep.append((cell, cells))
         checks.append((out, (cells == w["cell"]).astype(np.uint32)))
     t0 = time.perf_counter()
     vp.velopir_query_batch(ctx, recs, use_graph=True)
