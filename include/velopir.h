@@ -49,8 +49,9 @@ enum {
     VELOPIR_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
     VELOPIR_ERR_BUSY = -6,    /* serving queue full / ticket not finished */
     VELOPIR_ERR_NOCUDA = -7,  /* no CUDA device is visible */
-    VELOPIR_ERR_PLAN = -8     /* a dry run found a gate reading a value that was
+    VELOPIR_ERR_PLAN = -8,    /* a dry run found a gate reading a value that was
                                  not yet written or already overwritten */
+    VELOPIR_ERR_CANCELLED = -9 /* velopir_poll: the ticket was cancelled */
 };
 
 /* Gates (Section 2.2 names HomAND, HomXOR, HomXNOR; the others are tfhe-2's
@@ -325,6 +326,16 @@ int velopir_submit(velopir_ctx *ctx, const velopir_query *q, uint64_t *ticket);
  * whether `ticket` has finished (*done = 1; its result is in q->out).
  * Errors: ERR_ARG (unknown ticket), ERR_CUDA, ERR_TIMEOUT. */
 int velopir_poll(velopir_ctx *ctx, uint64_t ticket, int *done);
+
+/* Cancel a submitted query.  A waiting query is dropped at once; an admitted
+ * one gets no further launches, and its memory is released when the work
+ * already issued for it has finished.  The ticket is then reported like a
+ * finished one, and velopir_poll returns VELOPIR_ERR_CANCELLED for it (with
+ * *done = 1); its output is undefined.  Until then the query's buffers may
+ * still be read or written by work already on the device.  A query whose last
+ * layer is already issued completes normally.  Errors: ERR_ARG (unknown
+ * ticket), ERR_CUDA. */
+int velopir_cancel(velopir_ctx *ctx, uint64_t ticket);
 
 /* Advance the serving loop by at most one merged layer launch (admitting
  * waiting queries first) and report up to `cap` tickets that have finished

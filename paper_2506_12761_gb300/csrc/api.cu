@@ -448,6 +448,7 @@ struct ServeQuery {
     size_t out_words = 0;
     bool out_host = false;
     bool done = false;
+    bool cancelled = false; // velopir_cancel: issue nothing more, report as cancelled
     cudaEvent_t ev = nullptr;
 };
 
@@ -559,7 +560,7 @@ int serve_step(velopir_ctx *c)
     size_t total_br = 0;
     for (auto &sp : c->active) {
         ServeQuery &s = *sp;
-        if (s.cursor < s.P.layers.size()) {
+        if (!s.cancelled && s.cursor < s.P.layers.size()) {
             const Layer &L = s.P.layers[s.cursor];
             total_br += L.br.size() - (s.offset < L.ks.size() ? (size_t)L.ks[s.offset].e0 : L.br.size());
         }
@@ -582,7 +583,7 @@ int serve_step(velopir_ctx *c)
             }
             s.pre_done = true;
         }
-        if (s.cursor >= s.P.layers.size() || ML.br.size() >= take) continue;
+        if (s.cancelled || s.cursor >= s.P.layers.size() || ML.br.size() >= take) continue;
         const Layer &L = s.P.layers[s.cursor];
         // a gate's blind rotations are consecutive, in the order of its key switches
         for (; s.offset < L.ks.size(); ++s.offset) {
@@ -1131,6 +1132,31 @@ int velopir_submit(velopir_ctx *c, const velopir_query *q, uint64_t *ticket)
     return VELOPIR_OK;
 }
 
+int velopir_cancel(velopir_ctx *c, uint64_t ticket)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    cudaSetDevice(c->device);
+    for (auto it = c->waiting.begin(); it != c->waiting.end(); ++it)
+        if ((*it)->ticket == ticket) {   // never admitted: nothing on the device
+            (*it)->cancelled = true;
+            c->finished.push_back(std::move(*it));
+            c->waiting.erase(it);
+            return VELOPIR_OK;
+        }
+    for (auto &s : c->active)
+        if (s->ticket == ticket) {
+            if (!s->ev) {   // marks the end of the work already issued for it
+                s->cancelled = true;
+                CU(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+                CU(cudaEventRecord(s->ev, c->stream));
+            }
+            return VELOPIR_OK;   // finishing already (its last layer is issued): it completes normally
+        }
+    for (auto &s : c->finished)
+        if (s->ticket == ticket) return VELOPIR_OK;
+    return fail(c, VELOPIR_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+}
+
 int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
 {
     if (!c || !done) return fail(c, VELOPIR_ERR_ARG, "null argument");
@@ -1139,7 +1165,9 @@ int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
     for (auto it = c->finished.begin(); it != c->finished.end(); ++it)
         if ((*it)->ticket == ticket) {
             *done = 1;
+            const bool cancelled = (*it)->cancelled;
             c->finished.erase(it);
+            if (cancelled) return fail(c, VELOPIR_ERR_CANCELLED, "ticket %llu was cancelled", (unsigned long long)ticket);
             return VELOPIR_OK;
         }
     bool known = false;
@@ -1155,7 +1183,9 @@ int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
     for (auto it = c->finished.begin(); it != c->finished.end(); ++it)
         if ((*it)->ticket == ticket) {
             *done = 1;
+            const bool cancelled = (*it)->cancelled;
             c->finished.erase(it);
+            if (cancelled) return fail(c, VELOPIR_ERR_CANCELLED, "ticket %llu was cancelled", (unsigned long long)ticket);
             break;
         }
     return VELOPIR_OK;

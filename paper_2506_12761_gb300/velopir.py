@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "libvelopir.so")
 
 VELOPIR_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_NOKEY", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_BUSY",
-          -7: "ERR_NOCUDA", -8: "ERR_PLAN"}
+          -7: "ERR_NOCUDA", -8: "ERR_PLAN", -9: "ERR_CANCELLED"}
+ERRORS_BY_NAME = {v: k for k, v in ERRORS.items()}
 (VP_AND, VP_NAND, VP_OR, VP_NOR, VP_XOR, VP_XNOR, VP_ANDNY, VP_ANDYN, VP_ORNY, VP_ORYN, VP_MUX) = range(11)
 VP_PATH_INT32_DENSE, VP_PATH_NTT, VP_PATH_TENSOR_F16 = 0, 1, 2
 VP_QUERY_INTV, VP_QUERY_COV, VP_QUERY_IDM = 0, 1, 2
@@ -36,7 +37,7 @@ EXPORTS = [
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
     "velopir_selftest_wait_timeout", "velopir_plan_query", "velopir_client_pubkeygen", "velopir_server_encrypt",
-    "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb",
+    "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb", "velopir_cancel",
 ]
 NOALLOC_MAX_GATES = 256
 NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "velopir_id_match": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_submit": (i, [vp, ctypes.POINTER(Query), ctypes.POINTER(u64)]),
             "velopir_poll": (i, [vp, u64, ctypes.POINTER(i)]),
+            "velopir_cancel": (i, [vp, u64]),
             "velopir_queue_depth": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
             "velopir_progress": (i, [vp, ctypes.POINTER(u64), sz, ctypes.POINTER(sz)]),
             "velopir_sync": (i, [vp]),
@@ -222,6 +224,10 @@ def velopir_poll(ctx, ticket: int) -> bool:
     d = ctypes.c_int()
     _check(ctx, lib().velopir_poll(ctx, ticket, ctypes.byref(d)))
     return bool(d.value)
+
+
+def velopir_cancel(ctx, ticket: int) -> None:
+    _check(ctx, lib().velopir_cancel(ctx, ticket))
 
 
 def velopir_progress(ctx, cap: int = 256) -> list[int]:

@@ -146,3 +146,37 @@ def test_progress_reports_every_ticket_once():
     assert vp.velopir_progress(ctx.h) == []
     for q, a in zip(qs, alone):
         assert np.array_equal(q["out"], a)
+
+
+def test_cancel_waiting_and_admitted_queries():
+    """A query cancelled before admission, or while its layers run, is
+    reported once as cancelled (velopir_poll raises ERR_CANCELLED); the others
+    finish with the results they have alone, and admitted memory is released."""
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 7)            # IntV (34 layers), CoV, IdM
+    alone = [run_alone(ctx, q) for q in qs]
+    ts = [vp.velopir_submit(ctx.h, as_record(q)) for q in qs]
+    vp.velopir_cancel(ctx.h, ts[1])    # still waiting: dropped at once
+    with pytest.raises(vp.VelopirError) as e:
+        vp.velopir_poll(ctx.h, ts[1])
+    assert e.value.code == vp.ERRORS_BY_NAME["ERR_CANCELLED"]
+    assert vp.velopir_poll(ctx.h, ts[0]) is False   # admits the rest, issues one step
+    vp.velopir_cancel(ctx.h, ts[0])    # admitted, most layers still to go
+    done, cancelled = set(), set()
+    for _ in range(500):
+        for i in (0, 2):
+            if i in done or i in cancelled:
+                continue
+            try:
+                if vp.velopir_poll(ctx.h, ts[i]):
+                    done.add(i)
+            except vp.VelopirError as err:
+                assert err.code == vp.ERRORS_BY_NAME["ERR_CANCELLED"]
+                cancelled.add(i)
+        if len(done) + len(cancelled) == 2:
+            break
+    assert cancelled == {0} and done == {2}
+    assert np.array_equal(qs[2]["out"], alone[2])
+    assert vp.velopir_queue_depth(ctx.h) == (0, 0)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_cancel(ctx.h, 10 ** 9)
