@@ -290,6 +290,16 @@ int velopir_autotune(velopir_ctx *ctx, double *wave_ms_out, int n_out);
  * (>= 1 on success).  Errors: ERR_ARG. */
 int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
 
+/* Kinds accepted by velopir_plan_query only: the three modes over an
+ * encrypted database (the *_encdb calls).  q->id_bits is then the width
+ * (IntV l, CoV w, IdM id_bits), db and payload hold plaintext values (IntV
+ * [D][4], CoV [D] packed (y << w) | x, IdM [D]; payload [D], payload_bits
+ * <= 32), and the dry run encrypts every database bit as a ServerEnc
+ * ciphertext would be. */
+#define VP_PLAN_INTV_ENCDB 3
+#define VP_PLAN_COV_ENCDB 4
+#define VP_PLAN_IDM_ENCDB 5
+
 /* Host-only dry run of a query's launch plan; no GPU or context is used.
  * Builds the gate program of q (Section 5's circuits for IntV, CoV or IdM,
  * with q->kind, D, db, id_bits, payload and payload_bits as in the query
@@ -301,10 +311,11 @@ int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
  * message +-1/8 (Section 2.2 Ecd) and each bootstrap returns the message of
  * the sign of its pre-combined phase (phase 0 reads as true).
  *   bits_a: the query's plaintext bits, one uint32_t 0/1 per ciphertext of
- *           enc_a (IntV x[32], CoV cell[32], IdM id[id_bits]), LSB first;
- *   bits_b: IntV y[32], else ignored (nullable);
+ *           enc_a (IntV x[32] or x[l], CoV cell[32] or cell[2w], IdM
+ *           id[id_bits]), LSB first;
+ *   bits_b: IntV y[32] or y[l], else ignored (nullable);
  *   bits_out: receives one 0/1 per output ciphertext (D entries, or
- *             payload_bits for IdM with a payload);
+ *             payload_bits with a payload);
  *   launch_sizes (nullable): receives the blind rotations of each launch,
  *           up to max_launches entries.
  * Returns the number of launches (>= 1), VELOPIR_ERR_ARG for bad arguments,

@@ -18,11 +18,9 @@ using namespace vp;
 
 namespace {
 
-size_t plan_in_bits(const velopir_query &q) { return q.kind == VP_QUERY_IDM ? (size_t)q.id_bits : 32; }
-
 size_t plan_out_bits(const velopir_query &q)
 {
-    return (q.kind == VP_QUERY_IDM && q.payload) ? (size_t)q.payload_bits : q.D;
+    return q.payload ? (size_t)q.payload_bits : q.D;
 }
 
 struct Exec {
@@ -75,34 +73,62 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
                                   uint32_t *bits_out, size_t *launch_sizes, int max_launches)
 {
     if (!q || !q->db || q->D == 0 || !bits_a || !bits_out || wave < 0) return VELOPIR_ERR_ARG;
-    if (q->kind != VP_QUERY_INTV && q->kind != VP_QUERY_COV && q->kind != VP_QUERY_IDM) return VELOPIR_ERR_ARG;
-    if (q->kind == VP_QUERY_INTV && !bits_b) return VELOPIR_ERR_ARG;
-    if (q->kind == VP_QUERY_IDM && (q->id_bits < 1 || q->id_bits > 32)) return VELOPIR_ERR_ARG;
-    if (q->kind == VP_QUERY_IDM && q->payload && (q->payload_bits < 1 || q->payload_bits > 32)) return VELOPIR_ERR_ARG;
+    const int kind = q->kind;
+    const bool encdb = kind >= VP_PLAN_INTV_ENCDB && kind <= VP_PLAN_IDM_ENCDB;
+    if (kind != VP_QUERY_INTV && kind != VP_QUERY_COV && kind != VP_QUERY_IDM && !encdb) return VELOPIR_ERR_ARG;
+    if ((kind == VP_QUERY_INTV || kind == VP_PLAN_INTV_ENCDB) && !bits_b) return VELOPIR_ERR_ARG;
+    const int width = q->id_bits;
+    if ((kind == VP_QUERY_IDM || kind == VP_PLAN_INTV_ENCDB || kind == VP_PLAN_IDM_ENCDB) && (width < 1 || width > 32))
+        return VELOPIR_ERR_ARG;
+    if (kind == VP_PLAN_COV_ENCDB && (width < 1 || width > 16)) return VELOPIR_ERR_ARG;
+    if (q->payload && (q->payload_bits < 1 || q->payload_bits > 32)) return VELOPIR_ERR_ARG;
+    if (q->payload && (kind == VP_QUERY_INTV || kind == VP_QUERY_COV)) return VELOPIR_ERR_ARG;   // no payload form
     if (launch_sizes && max_launches < 0) return VELOPIR_ERR_ARG;
 
     // stand-in device addresses: distinct, 16-byte aligned, never dereferenced
     uint32_t *in_a = reinterpret_cast<uint32_t *>(uintptr_t(1) << 32);
     uint32_t *in_b = reinterpret_cast<uint32_t *>(uintptr_t(2) << 32);
     uint32_t *out = reinterpret_cast<uint32_t *>(uintptr_t(3) << 32);
+    uint32_t *edb = reinterpret_cast<uint32_t *>(uintptr_t(4) << 32);
+    uint32_t *epay = reinterpret_cast<uint32_t *>(uintptr_t(5) << 32);
+    // query and database widths, in ciphertexts
+    const size_t na = kind == VP_QUERY_IDM ? (size_t)width : kind == VP_PLAN_COV_ENCDB ? 2 * (size_t)width
+                      : encdb ? (size_t)width : 32;
+    const size_t nb = kind == VP_QUERY_INTV ? 32 : kind == VP_PLAN_INTV_ENCDB ? (size_t)width : 0;
+    const size_t per_entry = kind == VP_PLAN_INTV_ENCDB ? 4 * (size_t)width : na;   // database ciphertexts per entry
+    const int pb = q->payload ? q->payload_bits : 0;
     Program P;
     Builder B(P);
-    const size_t na = plan_in_bits(*q);
-    std::vector<Ref> a(32), b(32);
+    std::vector<Ref> a(na), b(nb);
     for (size_t i = 0; i < na; ++i) a[i] = B.input(in_a + i * kLweWords);
-    if (q->kind == VP_QUERY_INTV)
-        for (size_t i = 0; i < 32; ++i) b[i] = B.input(in_b + i * kLweWords);
-    if (q->kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), q->db, q->D, out);
-    else if (q->kind == VP_QUERY_COV) build_cov(B, a.data(), q->db, q->D, out);
-    else build_idm(B, a.data(), q->id_bits, q->db, q->D, q->payload, q->payload_bits, out);
+    for (size_t i = 0; i < nb; ++i) b[i] = B.input(in_b + i * kLweWords);
+    switch (kind) {
+    case VP_QUERY_INTV: build_intv(B, a.data(), b.data(), q->db, q->D, out); break;
+    case VP_QUERY_COV: build_cov(B, a.data(), q->db, q->D, out); break;
+    case VP_QUERY_IDM: build_idm(B, a.data(), width, q->db, q->D, q->payload, q->payload_bits, out); break;
+    case VP_PLAN_INTV_ENCDB:
+        build_intv_enc(B, a.data(), b.data(), width, edb, q->D, pb ? epay : nullptr, pb, out);
+        break;
+    case VP_PLAN_COV_ENCDB: build_cov_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out); break;
+    default: build_idm_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out); break;
+    }
     relayer(P, wave);
     allocate_slots(P);
 
     Exec X(P);
     auto enc = [](uint32_t bit) { return bit ? kMu : 0u - kMu; };
     for (size_t i = 0; i < na; ++i) X.write(in_a + i * kLweWords, enc(bits_a[i] & 1u));
-    if (q->kind == VP_QUERY_INTV)
-        for (size_t i = 0; i < 32; ++i) X.write(in_b + i * kLweWords, enc(bits_b[i] & 1u));
+    for (size_t i = 0; i < nb; ++i) X.write(in_b + i * kLweWords, enc(bits_b[i] & 1u));
+    if (encdb) {   // the database as ServerEnc would encrypt it, one ciphertext per bit, LSB first
+        const size_t vals = kind == VP_PLAN_INTV_ENCDB ? 4 : 1, bits = per_entry / vals;
+        for (size_t d = 0; d < q->D; ++d)
+            for (size_t v = 0; v < vals; ++v)
+                for (size_t i = 0; i < bits; ++i)
+                    X.write(edb + ((d * vals + v) * bits + i) * kLweWords, enc((q->db[d * vals + v] >> i) & 1u));
+        for (size_t d = 0; pb && d < q->D; ++d)
+            for (int i = 0; i < pb; ++i)
+                X.write(epay + (d * pb + i) * kLweWords, enc((q->payload[d] >> i) & 1u));
+    }
     X.free_jobs(P.pre);
     std::vector<uint32_t> ext;
     for (size_t l = 0; l < P.layers.size(); ++l) {

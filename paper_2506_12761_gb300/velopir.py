@@ -23,6 +23,7 @@ ERRORS_BY_NAME = {v: k for k, v in ERRORS.items()}
 (VP_AND, VP_NAND, VP_OR, VP_NOR, VP_XOR, VP_XNOR, VP_ANDNY, VP_ANDYN, VP_ORNY, VP_ORYN, VP_MUX) = range(11)
 VP_PATH_INT32_DENSE, VP_PATH_NTT, VP_PATH_TENSOR_F16 = 0, 1, 2
 VP_QUERY_INTV, VP_QUERY_COV, VP_QUERY_IDM = 0, 1, 2
+VP_PLAN_INTV_ENCDB, VP_PLAN_COV_ENCDB, VP_PLAN_IDM_ENCDB = 3, 4, 5   # velopir_plan_query only
 LWE_WORDS = 631
 BK_WORDS = 630 * 6 * 2 * 1024
 KSK_WORDS = 1024 * 8 * 4 * 631
@@ -330,7 +331,9 @@ class Context:
 
 def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0, id_bits: int = 0,
                        payload=None, payload_bits: int = 0, max_launches: int = 4096):
-    """Host-only dry run of a query's launch plan on plaintext bits.
+    """Host-only dry run of a query's launch plan on plaintext bits.  For the
+    VP_PLAN_*_ENCDB kinds id_bits is the width (l, w or id_bits) and db /
+    payload are plaintext values the dry run encrypts.
 
     Returns (result bits, blind rotations per launch).  Raises VelopirError
     (ERR_PLAN) if the plan reads a value before it is written or after its
@@ -340,7 +343,7 @@ def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0
     b = None if bits_b is None else np.ascontiguousarray(bits_b, dtype=np.uint32)
     pay = None if payload is None else np.ascontiguousarray(payload, dtype=np.uint32)
     q = Query(kind, id_bits, payload_bits, 0, None, None, ptr(db), ptr(pay), D, None)
-    nout = payload_bits if (kind == VP_QUERY_IDM and payload is not None) else D
+    nout = payload_bits if payload is not None else D
     out = np.zeros(max(1, nout), dtype=np.uint32)
     sizes = (ctypes.c_size_t * max_launches)()
     rc = lib().velopir_plan_query(ctypes.byref(q), wave, ptr(a), ptr(b), ptr(out), sizes, max_launches)

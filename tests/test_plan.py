@@ -117,3 +117,65 @@ def test_plan_rejects_bad_arguments():
         vp.velopir_plan_query(vp.VP_QUERY_INTV, np.zeros((4, 4), np.uint32), 4, bits(0, 32), None)
     with pytest.raises(vp.VelopirError):
         vp.velopir_plan_query(7, cells, 4, bits(0, 32))
+
+
+# ---- the encrypted-database circuits (the *_encdb calls) ----
+
+def xor_of(values, valid):
+    acc = 0
+    for v, ok in zip(values, valid):
+        acc ^= int(v) if ok else 0
+    return acc
+
+
+@pytest.mark.parametrize("wave", [0, 64])
+def test_intv_encdb_plan_at_the_papers_width(wave):
+    """l_I = 16 with encrypted bounds and a 9-bit encrypted payload (covid-kor's
+    shape, M larger): the HomCompLeOPT MUX ripple, HomBitwiseAND and HomSum."""
+    rng = np.random.default_rng(21)
+    D, l = 40, 16
+    u = rng.integers(0, 1 << l, size=(D, 4))
+    x, y = 40000, 1234
+    lo, hi = np.minimum(u[:, [0, 2]], u[:, [1, 3]]), np.maximum(u[:, [0, 2]], u[:, [1, 3]])
+    lo[::5], hi[::5] = [x - 3, y], [x + 1, y + 1]
+    rects = np.stack([lo[:, 0], hi[:, 0], lo[:, 1], hi[:, 1]], axis=1).astype(np.uint32)
+    valid = (rects[:, 0] <= x) & (x < rects[:, 1]) & (rects[:, 2] <= y) & (y < rects[:, 3])
+    out, sizes = vp.velopir_plan_query(vp.VP_PLAN_INTV_ENCDB, rects, D, bits(x, l), bits(y, l), wave=wave, id_bits=l)
+    assert np.array_equal(out, valid.astype(np.uint32)) and 0 < valid.sum() < D
+    launches_are_waves(sizes, wave, (12 * l + 3) * D)
+    pay = rng.integers(0, 1 << 9, size=D).astype(np.uint32)
+    agg, sizes = vp.velopir_plan_query(vp.VP_PLAN_INTV_ENCDB, rects, D, bits(x, l), bits(y, l), wave=wave, id_bits=l,
+                                       payload=pay, payload_bits=9)
+    assert np.array_equal(agg, bits(xor_of(pay, valid), 9))
+    launches_are_waves(sizes, wave, (12 * l + 3) * D + 9 * D + 9 * (D - 1))
+
+
+def test_encdb_comparator_boundaries_exhaustive():
+    """Every (bound, point) pair at l = 4 through the encrypted comparators:
+    rectangles [a, b) x [0, 15) with the point on and around the bounds."""
+    l = 4
+    for x in range(16):
+        rects = np.array([[a, b, 0, 15] for a in range(16) for b in range(16)], dtype=np.uint32)
+        out, _ = vp.velopir_plan_query(vp.VP_PLAN_INTV_ENCDB, rects, len(rects), bits(x, l), bits(3, l),
+                                       wave=0, id_bits=l)
+        want = ((rects[:, 0] <= x) & (x < rects[:, 1])).astype(np.uint32)
+        assert np.array_equal(out, want), x
+
+
+@pytest.mark.parametrize("wave", [0, 48])
+def test_cov_and_idm_encdb_plans(wave):
+    rng = np.random.default_rng(22)
+    w = 16
+    cells = rng.integers(0, 1 << 32, size=30, dtype=np.uint64).astype(np.uint32)
+    q = int(cells[11])
+    cells[12] = q ^ (1 << 20)
+    out, _ = vp.velopir_plan_query(vp.VP_PLAN_COV_ENCDB, cells, 30, bits(q, 2 * w), wave=wave, id_bits=w)
+    assert np.array_equal(out, (cells == q).astype(np.uint32))
+    ids = rng.choice(1 << 16, size=50, replace=False).astype(np.uint32)
+    pay = rng.integers(0, 1 << 32, size=50, dtype=np.uint64).astype(np.uint32)
+    agg, sizes = vp.velopir_plan_query(vp.VP_PLAN_IDM_ENCDB, ids, 50, bits(int(ids[7]), 16), wave=wave, id_bits=16,
+                                       payload=pay, payload_bits=32)
+    assert np.array_equal(agg, bits(int(pay[7]), 32))
+    launches_are_waves(sizes, wave, 31 * 50 + 32 * 50 + 32 * 49)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_PLAN_COV_ENCDB, cells, 30, bits(q, 34), id_bits=17)
