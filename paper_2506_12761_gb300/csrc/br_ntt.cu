@@ -21,8 +21,9 @@
 //
 // Layout: one warp owns one bootstrap.  A 1024-point transform lives in the
 // warp's registers, 32 points per lane; the five stages whose pairs lie in
-// one lane run in registers, a padded 32x33 shared-memory transpose moves to
-// the other lane grouping, and five more stages run in registers.  No block
+// one lane run in registers, a 32x32 shared-memory transpose (16-byte rows
+// XOR-swizzled) moves to the other lane grouping, and five more stages run in
+// registers.  No block
 // barrier is involved: each warp synchronises only itself.  Warp 0 also
 // streams the transformed key in 16 KB chunks (one step, prime and row) into a
 // ring with bulk asynchronous copies; full/empty mbarriers hand the chunks
