@@ -333,10 +333,24 @@ void relayer(Program &p, int wave)
     if (wave <= 0 || p.layers.size() <= 1) return;
     struct G {
         int layer, ks, nbr, height = 1, indeg = 0, at = -1;
-        std::vector<int> succ;
     };
     std::vector<G> g;
-    std::unordered_map<uint64_t, int> producer;   // output address (slot tag or device) -> gate
+    // Producer of each readable value: pool slots are dense indices (a flat
+    // table); device addresses (outputs into caller buffers) are few (a map).
+    std::vector<int> slot_prod(p.slot_def.size(), -1);
+    std::unordered_map<uint64_t, int> addr_prod;
+    auto set_prod = [&](const void *a, int gate) {
+        const uint64_t v = (uint64_t)(uintptr_t)a;
+        if (v & kSlotTag) slot_prod[v & ~kSlotTag] = gate;
+        else addr_prod[v] = gate;
+    };
+    auto prod_of = [&](const void *a) -> int {
+        const uint64_t v = (uint64_t)(uintptr_t)a;
+        if (!v) return -1;
+        if (v & kSlotTag) return slot_prod[v & ~kSlotTag];
+        auto it = addr_prod.find(v);
+        return it == addr_prod.end() ? -1 : it->second;
+    };
     for (int l = 0; l < (int)p.layers.size(); ++l) {
         const Layer &L = p.layers[l];
         for (int k = 0; k < (int)L.ks.size(); ++k) {
@@ -344,41 +358,48 @@ void relayer(Program &p, int wave)
             x.layer = l;
             x.ks = k;
             x.nbr = L.ks[k].e1 >= 0 ? 2 : 1;
-            producer[(uint64_t)(uintptr_t)L.ks[k].out] = (int)g.size();
-            g.push_back(std::move(x));
+            set_prod(L.ks[k].out, (int)g.size());
+            g.push_back(x);
         }
         // a free job's output is ready with its input's producer
         for (const FreeJob &f : L.fr) {
-            auto it = f.in ? producer.find((uint64_t)(uintptr_t)f.in) : producer.end();
-            if (it != producer.end()) producer[(uint64_t)(uintptr_t)f.out] = it->second;
+            const int q = prod_of(f.in);
+            if (q >= 0) set_prod(f.out, q);
         }
     }
     const int ng = (int)g.size();
+    // predecessors (at most 4: two rotations x two inputs), then successors in CSR form
+    std::vector<int> pred(4 * (size_t)ng, -1);
+    std::vector<int> nsucc(ng + 1, 0);
     for (int i = 0; i < ng; ++i) {
         const Layer &L = p.layers[g[i].layer];
         const KsJob &k = L.ks[g[i].ks];
-        int preds[4], np = 0;
+        int np = 0;
         for (int e : {k.e0, k.e1}) {
             if (e < 0) continue;
             for (const uint32_t *in : {L.br[e].in0, L.br[e].in1}) {
-                if (!in) continue;
-                auto it = producer.find((uint64_t)(uintptr_t)in);
-                if (it == producer.end() || it->second == i) continue;
+                const int q = prod_of(in);
+                if (q < 0 || q == i) continue;
                 bool dup = false;
-                for (int q = 0; q < np; ++q) dup |= preds[q] == it->second;
-                if (!dup) preds[np++] = it->second;
+                for (int t = 0; t < np; ++t) dup |= pred[4 * (size_t)i + t] == q;
+                if (!dup) pred[4 * (size_t)i + np++] = q;
             }
         }
-        for (int q = 0; q < np; ++q) {
-            g[preds[q]].succ.push_back(i);
-            g[i].indeg++;
-        }
+        g[i].indeg = np;
+        for (int t = 0; t < np; ++t) nsucc[pred[4 * (size_t)i + t] + 1]++;
+    }
+    for (int i = 0; i < ng; ++i) nsucc[i + 1] += nsucc[i];
+    std::vector<int> succ(nsucc[ng]);
+    {
+        std::vector<int> fill(nsucc.begin(), nsucc.end() - 1);
+        for (int i = 0; i < ng; ++i)
+            for (int t = 0; t < 4 && pred[4 * (size_t)i + t] >= 0; ++t) succ[fill[pred[4 * (size_t)i + t]]++] = i;
     }
     // longest chain of gates from each gate to the end (producers precede
     // consumers in the ASAP order, so a reverse sweep sees successors first)
     int hmax = 1;
     for (int i = ng - 1; i >= 0; --i) {
-        for (int s : g[i].succ) g[i].height = std::max(g[i].height, 1 + g[s].height);
+        for (int e = nsucc[i]; e < nsucc[i + 1]; ++e) g[i].height = std::max(g[i].height, 1 + g[succ[e]].height);
         hmax = std::max(hmax, g[i].height);
     }
     std::vector<std::deque<int>> ready(hmax + 1);
@@ -408,8 +429,8 @@ void relayer(Program &p, int wave)
         next.clear();
         for (int i : take) {
             g[i].at = t;
-            for (int s : g[i].succ)
-                if (--g[s].indeg == 0) next.push_back(s);
+            for (int e = nsucc[i]; e < nsucc[i + 1]; ++e)
+                if (--g[succ[e]].indeg == 0) next.push_back(succ[e]);
         }
         for (int s : next) { ready[g[s].height].push_back(s); nready += g[s].nbr; }
         done += (int)take.size();
@@ -417,14 +438,22 @@ void relayer(Program &p, int wave)
     }
 
     // rebuild the layers, the free jobs after their producer's layer, and slot liveness
-    std::vector<std::vector<FreeJob>> fr_of(ng);
+    // free jobs of each producer gate (usually none): a sorted list
+    std::vector<std::pair<int, FreeJob>> fr_of;
     for (const Layer &L : p.layers)
         for (const FreeJob &f : L.fr) {
-            auto it = f.in ? producer.find((uint64_t)(uintptr_t)f.in) : producer.end();
-            if (it != producer.end()) fr_of[it->second].push_back(f);
+            const int q = prod_of(f.in);
+            if (q >= 0) fr_of.emplace_back(q, f);
             else p.pre.push_back(f);
         }
+    std::stable_sort(fr_of.begin(), fr_of.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
     std::vector<Layer> NL(sched.size());
+    for (size_t t = 0; t < sched.size(); ++t) {
+        size_t nbr = 0;
+        for (int i : sched[t]) nbr += g[i].nbr;
+        NL[t].br.reserve(nbr);
+        NL[t].ks.reserve(sched[t].size());
+    }
     for (size_t t = 0; t < sched.size(); ++t)
         for (int i : sched[t]) {
             const Layer &L = p.layers[g[i].layer];
@@ -435,7 +464,9 @@ void relayer(Program &p, int wave)
             k.e0 = e0;
             k.e1 = k.e1 >= 0 ? e0 + 1 : -1;
             NL[t].ks.push_back(k);
-            for (const FreeJob &f : fr_of[i]) NL[t].fr.push_back(f);
+            auto it = std::lower_bound(fr_of.begin(), fr_of.end(), i,
+                                       [](const std::pair<int, FreeJob> &a, int v) { return a.first < v; });
+            for (; it != fr_of.end() && it->first == i; ++it) NL[t].fr.push_back(it->second);
         }
     p.layers.swap(NL);
     auto slot_of = [](const void *a) { return ((uint64_t)(uintptr_t)a & kSlotTag) ? (int)((uint64_t)(uintptr_t)a & ~kSlotTag) : -1; };
