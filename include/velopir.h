@@ -324,6 +324,19 @@ int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
 int velopir_plan_query(const velopir_query *q, int wave, const uint32_t *bits_a, const uint32_t *bits_b,
                        uint32_t *bits_out, size_t *launch_sizes, int max_launches);
 
+/* Host-only dry run of a batch of queries as velopir_query_batch runs them:
+ * one merged gate program over all queries, scheduled as in
+ * velopir_plan_query, executed in the device's launch order -- each launch
+ * split into chunks of at most chunk_rows blind rotations (0: no split;
+ * the executor splits at 65,536), every chunk's blind rotations before its
+ * key switches -- on noiseless plaintext phases.  Plaintext-database kinds
+ * (VP_QUERY_*) only.  bits_a, bits_b and bits_out are the per-query arrays
+ * of velopir_plan_query concatenated in query order (bits_b holds the IntV
+ * queries' y bits only).  Returns the number of launches, ERR_ARG, or
+ * ERR_PLAN as velopir_plan_query. */
+int velopir_plan_batch(const velopir_query *qs, size_t nq, int wave, int chunk_rows, const uint32_t *bits_a,
+                       const uint32_t *bits_b, uint32_t *bits_out, size_t *launch_sizes, int max_launches);
+
 /* ---- serving: asynchronous queries with continuous batching ------------- */
 
 /* Enqueue a query.  It is admitted into the running batch as soon as the

@@ -8,6 +8,7 @@
 // as on the device.  Each physical pool slot remembers which value it holds,
 // so a read of a value that is not yet written, or already overwritten, is
 // reported instead of silently computed.
+#include <algorithm>
 #include <unordered_map>
 #include <vector>
 
@@ -67,7 +68,104 @@ struct Exec {
     }
 };
 
+// Execute a scheduled program in the device's launch order: each launch is
+// split into chunks of at most chunk_rows blind rotations (0: one chunk), as
+// the executor splits launches to fit its extracted-row scratch, and every
+// chunk's blind rotations read before its key switches write.
+void execute(const Program &P, Exec &X, int chunk_rows, size_t *launch_sizes, int max_launches)
+{
+    X.free_jobs(P.pre);
+    std::vector<uint32_t> ext;
+    for (size_t l = 0; l < P.layers.size(); ++l) {
+        const Layer &L = P.layers[l];
+        const size_t nks = L.ks.size();
+        size_t g = 0;
+        while (g < nks) {
+            const int br0 = L.ks[g].e0;
+            size_t g1 = g;
+            int br1 = br0;
+            while (g1 < nks) {
+                const int hi = std::max(L.ks[g1].e0, L.ks[g1].e1) + 1;
+                if (chunk_rows > 0 && hi - br0 > chunk_rows && g1 > g) break;
+                br1 = std::max(br1, hi);
+                ++g1;
+            }
+            ext.assign((size_t)(br1 - br0), 0u);
+            for (int r = br0; r < br1; ++r) {
+                const BrJob &j = L.br[r];
+                const uint32_t c = j.cst + (uint32_t)j.s0 * X.read(j.in0) + (uint32_t)j.s1 * X.read(j.in1);
+                ext[r - br0] = (int32_t)c >= 0 ? kMu : 0u - kMu;
+            }
+            for (size_t q = g; q < g1; ++q) {
+                const KsJob &k = L.ks[q];
+                X.write(k.out, ext[k.e0 - br0] + (k.e1 >= 0 ? ext[k.e1 - br0] : 0u) + k.cst);
+            }
+            g = g1;
+        }
+        X.free_jobs(L.fr);
+        if (launch_sizes && (int)l < max_launches) launch_sizes[l] = L.br.size();
+    }
+}
+
+bool plain_kind_ok(const velopir_query &q)
+{
+    if (!q.db || q.D == 0) return false;
+    if (q.kind != VP_QUERY_INTV && q.kind != VP_QUERY_COV && q.kind != VP_QUERY_IDM) return false;
+    if (q.kind == VP_QUERY_IDM && (q.id_bits < 1 || q.id_bits > 32)) return false;
+    if (q.payload && (q.kind != VP_QUERY_IDM || q.payload_bits < 1 || q.payload_bits > 32)) return false;
+    return true;
+}
+
 }  // namespace
+
+extern "C" int velopir_plan_batch(const velopir_query *qs, size_t nq, int wave, int chunk_rows, const uint32_t *bits_a,
+                                  const uint32_t *bits_b, uint32_t *bits_out, size_t *launch_sizes, int max_launches)
+{
+    if (!qs || !nq || !bits_a || !bits_out || wave < 0 || chunk_rows < 0) return VELOPIR_ERR_ARG;
+    if (launch_sizes && max_launches < 0) return VELOPIR_ERR_ARG;
+    for (size_t i = 0; i < nq; ++i) {
+        if (!plain_kind_ok(qs[i])) return VELOPIR_ERR_ARG;
+        if (qs[i].kind == VP_QUERY_INTV && !bits_b) return VELOPIR_ERR_ARG;
+    }
+    // stand-in device addresses: each query's inputs and outputs in regions of their own
+    const uintptr_t in_base = uintptr_t(1) << 36, out_base = uintptr_t(2) << 36;
+    Program P;
+    Builder B(P);
+    std::vector<std::pair<uint32_t *, uint32_t>> inputs;   // address, bit
+    std::vector<uint32_t *> outs;
+    size_t ia = 0, ib = 0, ino = 0, outo = 0;
+    for (size_t i = 0; i < nq; ++i) {
+        const velopir_query &q = qs[i];
+        const size_t na = q.kind == VP_QUERY_IDM ? (size_t)q.id_bits : 32;
+        const size_t nb = q.kind == VP_QUERY_INTV ? 32 : 0;
+        uint32_t *in = reinterpret_cast<uint32_t *>(in_base) + ino;
+        uint32_t *out = reinterpret_cast<uint32_t *>(out_base) + outo;
+        std::vector<Ref> a(na), b(nb);
+        for (size_t k = 0; k < na; ++k) {
+            a[k] = B.input(in + k * kLweWords);
+            inputs.emplace_back(in + k * kLweWords, bits_a[ia++] & 1u);
+        }
+        for (size_t k = 0; k < nb; ++k) {
+            b[k] = B.input(in + (na + k) * kLweWords);
+            inputs.emplace_back(in + (na + k) * kLweWords, bits_b[ib++] & 1u);
+        }
+        if (q.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), q.db, q.D, out);
+        else if (q.kind == VP_QUERY_COV) build_cov(B, a.data(), q.db, q.D, out);
+        else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out);
+        const size_t nout = plan_out_bits(q);
+        for (size_t k = 0; k < nout; ++k) outs.push_back(out + k * kLweWords);
+        ino += (na + nb) * kLweWords;
+        outo += nout * kLweWords;
+    }
+    relayer(P, wave);
+    allocate_slots(P);
+    Exec X(P);
+    for (auto &w : inputs) X.write(w.first, w.second ? kMu : 0u - kMu);
+    execute(P, X, chunk_rows, launch_sizes, max_launches);
+    for (size_t k = 0; k < outs.size(); ++k) bits_out[k] = (int32_t)X.read(outs[k]) >= 0 ? 1u : 0u;
+    if (X.bad) return VELOPIR_ERR_PLAN;
+    return (int)P.layers.size();
+}
 
 extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32_t *bits_a, const uint32_t *bits_b,
                                   uint32_t *bits_out, size_t *launch_sizes, int max_launches)
@@ -129,21 +227,7 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
             for (int i = 0; i < pb; ++i)
                 X.write(epay + (d * pb + i) * kLweWords, enc((q->payload[d] >> i) & 1u));
     }
-    X.free_jobs(P.pre);
-    std::vector<uint32_t> ext;
-    for (size_t l = 0; l < P.layers.size(); ++l) {
-        const Layer &L = P.layers[l];
-        // every blind rotation of a launch reads before any key switch writes
-        ext.resize(L.br.size());
-        for (size_t r = 0; r < L.br.size(); ++r) {
-            const BrJob &j = L.br[r];
-            const uint32_t c = j.cst + (uint32_t)j.s0 * X.read(j.in0) + (uint32_t)j.s1 * X.read(j.in1);
-            ext[r] = (int32_t)c >= 0 ? kMu : 0u - kMu;
-        }
-        for (const KsJob &k : L.ks) X.write(k.out, ext[k.e0] + (k.e1 >= 0 ? ext[k.e1] : 0u) + k.cst);
-        X.free_jobs(L.fr);
-        if (launch_sizes && (int)l < max_launches) launch_sizes[l] = L.br.size();
-    }
+    execute(P, X, 0, launch_sizes, max_launches);
     const size_t nout = plan_out_bits(*q);
     for (size_t i = 0; i < nout; ++i) bits_out[i] = (int32_t)X.read(out + i * kLweWords) >= 0 ? 1u : 0u;
     if (X.bad) return VELOPIR_ERR_PLAN;

@@ -39,6 +39,7 @@ EXPORTS = [
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
     "velopir_selftest_wait_timeout", "velopir_plan_query", "velopir_client_pubkeygen", "velopir_server_encrypt",
     "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb", "velopir_cancel",
+    "velopir_plan_batch",
 ]
 NOALLOC_MAX_GATES = 256
 NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
@@ -105,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "velopir_autotune": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
             "velopir_tuned_shape": (i, [vp, sz]),
             "velopir_plan_query": (i, [ctypes.POINTER(Query), i, vp, vp, vp, ctypes.POINTER(sz), i]),
+            "velopir_plan_batch": (i, [ctypes.POINTER(Query), sz, i, i, vp, vp, vp, ctypes.POINTER(sz), i]),
             "velopir_client_pubkeygen": (i, [vp, vp, vp, sz, vp]),
             "velopir_server_encrypt": (i, [vp, vp, sz, vp]),
             "velopir_interval_query_encdb": (i, [vp, vp, vp, i, vp, sz, vp, i, vp]),
@@ -388,3 +390,31 @@ def velopir_coordinate_query_encdb(ctx, enc_cell, w: int, enc_cells, D: int, enc
 def velopir_id_match_encdb(ctx, enc_id, id_bits: int, enc_ids, D: int, enc_payload, payload_bits: int, out) -> None:
     _check(ctx, lib().velopir_id_match_encdb(ctx, ptr(enc_id), id_bits, ptr(enc_ids), D, ptr(enc_payload),
                                              payload_bits, ptr(out)))
+
+
+def velopir_plan_batch(queries, wave: int = 0, chunk_rows: int = 0, max_launches: int = 4096):
+    """Host-only dry run of a query batch (velopir_query_batch's program) on
+    plaintext bits.  queries: dicts with kind, db, D, bits_a, optional bits_b
+    (IntV), id_bits, payload, payload_bits.  Returns (per-query result bits,
+    blind rotations per launch)."""
+    keep, recs, a, b, nout = [], [], [], [], []
+    for q in queries:
+        db = np.ascontiguousarray(q["db"], dtype=np.uint32)
+        pay = None if q.get("payload") is None else np.ascontiguousarray(q["payload"], dtype=np.uint32)
+        keep += [db, pay]
+        recs.append(Query(q["kind"], q.get("id_bits", 0), q.get("payload_bits", 0) if pay is not None else 0, 0,
+                          None, None, ptr(db), ptr(pay), q["D"], None))
+        a.append(np.asarray(q["bits_a"], dtype=np.uint32))
+        if q["kind"] == VP_QUERY_INTV:
+            b.append(np.asarray(q["bits_b"], dtype=np.uint32))
+        nout.append(q["payload_bits"] if pay is not None else q["D"])
+    A = np.ascontiguousarray(np.concatenate(a))
+    Bb = np.ascontiguousarray(np.concatenate(b)) if b else None
+    out = np.zeros(max(1, sum(nout)), dtype=np.uint32)
+    sizes = (ctypes.c_size_t * max_launches)()
+    arr = (Query * len(recs))(*recs)
+    rc = lib().velopir_plan_batch(arr, len(recs), wave, chunk_rows, ptr(A), ptr(Bb), ptr(out), sizes, max_launches)
+    if rc < 0:
+        raise VelopirError(rc, "velopir_plan_batch")
+    splits = np.cumsum([0] + nout)
+    return [out[splits[k]:splits[k + 1]] for k in range(len(nout))], [int(sizes[k]) for k in range(min(rc, max_launches))]

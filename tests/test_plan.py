@@ -179,3 +179,37 @@ def test_cov_and_idm_encdb_plans(wave):
     launches_are_waves(sizes, wave, 31 * 50 + 32 * 50 + 32 * 49)
     with pytest.raises(vp.VelopirError):
         vp.velopir_plan_query(vp.VP_PLAN_COV_ENCDB, cells, 30, bits(q, 34), id_bits=17)
+
+
+def test_batch_of_uneven_queries_in_chunked_launch_order():
+    """velopir_query_batch's merged program over many queries of all three
+    modes (uneven sizes), with wave-filling, executed in the device's order
+    with launches split into small chunks: every query's answer is its
+    plaintext predicate and no slot is read after reuse."""
+    rng = np.random.default_rng(31)
+    qs, want = [], []
+    for k in range(12):
+        mode = k % 3
+        D = int(rng.integers(20, 400))
+        if mode == 0:
+            rects, bx, by, w = intv_case(D, 100 + k)
+            qs.append(dict(kind=vp.VP_QUERY_INTV, db=rects, D=D, bits_a=bx, bits_b=by))
+            want.append(w)
+        elif mode == 1:
+            cells = rng.integers(0, 1 << 32, size=D, dtype=np.uint64).astype(np.uint32)
+            q = int(cells[D // 2])
+            qs.append(dict(kind=vp.VP_QUERY_COV, db=cells, D=D, bits_a=bits(q, 32)))
+            want.append((cells == q).astype(np.uint32))
+        else:
+            ids = rng.choice(1 << 20, size=D, replace=False).astype(np.uint32)
+            pay = rng.integers(0, 1 << 32, size=D, dtype=np.uint64).astype(np.uint32)
+            qs.append(dict(kind=vp.VP_QUERY_IDM, db=ids, D=D, bits_a=bits(int(ids[3]), 20), id_bits=20,
+                           payload=pay, payload_bits=32))
+            want.append(np.array(bits(int(pay[3]), 32), dtype=np.uint32))
+    for wave, chunk in ((0, 0), (96, 500), (1824, 64)):
+        outs, sizes = vp.velopir_plan_batch(qs, wave=wave, chunk_rows=chunk)
+        for o, w in zip(outs, want):
+            assert np.array_equal(o, w)
+        launches_are_waves(sizes, wave, sum(131 * q["D"] if q["kind"] == vp.VP_QUERY_INTV else
+                                            31 * q["D"] if q["kind"] == vp.VP_QUERY_COV else
+                                            19 * q["D"] + 32 * (q["D"] - 1) for q in qs))
