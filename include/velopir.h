@@ -164,7 +164,8 @@ int velopir_bootstrap_plain(velopir_ctx *ctx, velopir_gate gate, const uint32_t 
  *                 x_lo <= x < x_hi AND y_lo <= y < y_hi (half-open, Theorem bb1).
  * Comparators follow Alg. HomCompLeOPT with XNOR/MUX against plaintext bits
  * rewritten into single gates and the top bit flipped for unsigned order;
- * 131 bootstraps per entry issued as 34 batched layers.
+ * 131 bootstraps per entry in 34 gate layers; the list scheduler launches
+ * the ready gates of all entries as whole waves of the blind-rotation kernel.
  * Errors: ERR_ARG, ERR_NOKEY, ERR_OOM, ERR_CUDA, ERR_TIMEOUT. */
 int velopir_interval_query(velopir_ctx *ctx, const uint32_t *enc_x, const uint32_t *enc_y,
                            const uint32_t *rects, size_t D, uint32_t *out_bits);
@@ -173,7 +174,7 @@ int velopir_interval_query(velopir_ctx *ctx, const uint32_t *enc_x, const uint32
  *   enc_cell: uint32_t[32][631]: bits 0..15 encrypt x, bits 16..31 encrypt y.
  *   cells   : uint32_t[D], packed (y << 16) | x.
  *   out_bits: uint32_t[D][631]; entry d encrypts (x, y) == cell d.
- * 31 bootstraps per entry in 5 batched layers.  Errors as above. */
+ * 31 bootstraps per entry in 5 gate layers.  Errors as above. */
 int velopir_coordinate_query(velopir_ctx *ctx, const uint32_t *enc_cell, const uint32_t *cells,
                              size_t D, uint32_t *out_bits);
 
