@@ -86,6 +86,10 @@ def lib():
             "orc_cov_batch": (None, [P, u32p, u32p, u32p, i, u64p, i64, u32p, i]),
             "orc_zero_out_plain": (None, [i, u32p, i, u32p]),
             "orc_homsum_tree": (None, [P, u32p, u32p, u32p, i64, i, i]),
+            "orc_gate_linear": (None, [P, u32p, u32p, i, i, i32p, u32p, u32p, u32, u32p]),
+            "orc_gate_linear_batch": (None, [P, u32p, u32p, i64, i32p, i32p, i32p, u32p, u32p, u32p, u32p, i]),
+            "orc_xor_many": (None, [P, u32p, u32p, u32p, i, u32p]),
+            "orc_homsum_tree_fanin": (None, [P, u32p, u32p, u32p, i64, i, i, i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -379,9 +383,51 @@ def homsum_tree(keys: Keys, S, threads: int | None = None) -> np.ndarray:
     return S[0].copy()
 
 
-def idm_payload(keys: Keys, x_cts, ids, payload, payload_bits: int = 32, threads: int | None = None) -> np.ndarray:
+def homsum_tree_fanin(keys: Keys, S, g: int, threads: int | None = None) -> np.ndarray:
+    """S: [M][lS][n+1]; the fan-in-g XOR tree (one bootstrap per g inputs).
+    Returns the aggregated [lS][n+1]; g = 2 is homsum_tree."""
+    P = keys.P
+    S = _u32(S).copy()
+    M, lS = S.shape[0], S.shape[1]
+    if M:
+        lib().orc_homsum_tree_fanin(ctypes.byref(P), _p(keys.bk), _p(keys.ksk), _p(S), M, lS, int(g),
+                                    threads or default_threads())
+    return S[0].copy()
+
+
+def xor_many(keys: Keys, cts) -> np.ndarray:
+    """XOR of g ciphertexts [g][n+1] with one bootstrap of 2 sum c_k + T((g-1)/4)."""
+    P = keys.P
+    c = _u32(cts)
+    out = np.zeros(P.n + 1, dtype=np.uint32)
+    lib().orc_xor_many(ctypes.byref(P), _p(keys.bk), _p(keys.ksk), _p(c), c.shape[0], _p(out))
+    return out
+
+
+def gate_linear_batch(keys: Keys, nrot, nin, coef, cst, ks_cst, inputs, threads: int | None = None) -> np.ndarray:
+    """Gates given by their pre-combinations: rotation r of gate g blind-rotates
+    sum_k coef[g][r][k] inputs[g][k] + T(cst[g][r]); the extractions are summed
+    with T(ks_cst[g]) and key-switched.  nrot, nin, ks_cst: [count];
+    coef: [count][2][8]; cst: [count][2]; inputs: [count][8][n+1]."""
+    P = keys.P
+    i32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    nrot, nin, coef = i32(nrot), i32(nin), i32(coef)
+    cst, ks_cst, inputs = _u32(cst), _u32(ks_cst), _u32(inputs)
+    count = nrot.shape[0]
+    assert coef.shape == (count, 2, 8) and cst.shape == (count, 2) and inputs.shape == (count, 8, P.n + 1)
+    out = np.zeros((count, P.n + 1), dtype=np.uint32)
+    if count:
+        lib().orc_gate_linear_batch(ctypes.byref(P), _p(keys.bk), _p(keys.ksk), count, _p(nrot, ctypes.c_int32),
+                                    _p(nin, ctypes.c_int32), _p(coef, ctypes.c_int32), _p(cst), _p(ks_cst),
+                                    _p(inputs), _p(out), threads or default_threads())
+    return out
+
+
+def idm_payload(keys: Keys, x_cts, ids, payload, payload_bits: int = 32, threads: int | None = None,
+                fanin: int = 2) -> np.ndarray:
     """IdM with a plaintext payload per entry: match bits, free zero-out with
-    each payload bit, then the HomSum XOR tree.  Returns [payload_bits][n+1]."""
+    each payload bit, then the HomSum XOR tree (pairwise, or fan-in g with one
+    bootstrap per g inputs).  Returns [payload_bits][n+1]."""
     P = keys.P
     v = idm_batch(keys, x_cts, ids, threads)
     pay = np.asarray(payload, dtype=np.uint64).reshape(-1)
@@ -390,7 +436,9 @@ def idm_payload(keys: Keys, x_cts, ids, payload, payload_bits: int = 32, threads
     for d in range(D):
         for j in range(payload_bits):
             S[d, j] = zero_out_plain(v[d], int((int(pay[d]) >> j) & 1))
-    return homsum_tree(keys, S, threads)
+    if fanin == 2:
+        return homsum_tree(keys, S, threads)
+    return homsum_tree_fanin(keys, S, fanin, threads)
 
 
 # --------------------------------------------------------------------------

@@ -603,3 +603,104 @@ void orc_homsum_tree(const orc_params *P, const uint32_t *bk, const uint32_t *ks
         }
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* A gate given by its linear pre-combinations.                              */
+/* ------------------------------------------------------------------------- */
+
+/* Section 2.2 writes a bootstrapped gate as Bootstrap(T(c) + a linear
+ * combination of its input ciphertexts); tfhe-2's MUX blind-rotates two such
+ * combinations and sums their extractions before one key switch.  This is
+ * that definition with the combination spelled out: rotation r < nrot
+ * blind-rotates c_r = sum_{k < nin} coef[r][k] * in_k + T(cst[r]) (test
+ * vector 1/8) and extracts it; the extractions are summed, T(ks_cst) is
+ * added to b, and the sum is key-switched.  coef = [2][8], in = [nin][n+1].
+ * Pin: decryption against the sign of the noiseless combined phase, and
+ * equality with orc_gate for the ten gates and MUX. */
+void orc_gate_linear(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int nrot, int nin,
+                     const int32_t *coef, const uint32_t *cst, const uint32_t *in, uint32_t ks_cst,
+                     uint32_t *out)
+{
+    const int n = P->n, N = P->N;
+    uint32_t *c = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    uint32_t *acc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)N);
+    uint32_t *big = (uint32_t *)calloc((size_t)N + 1, sizeof(uint32_t));
+    uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)N + 1));
+    for (int r = 0; r < nrot; r++) {
+        memset(c, 0, sizeof(uint32_t) * ((size_t)n + 1));
+        for (int k = 0; k < nin; k++)
+            for (int i = 0; i <= n; i++) c[i] += (uint32_t)coef[r * 8 + k] * in[(size_t)k * (n + 1) + i];
+        c[n] += cst[r];
+        orc_blind_rotate(P, bk, c, MU_1_8, acc, 1);
+        orc_sample_extract(N, acc, ext);
+        for (int i = 0; i <= N; i++) big[i] += ext[i];
+    }
+    big[N] += ks_cst;
+    orc_key_switch(P, ksk, big, out);
+    free(c); free(acc); free(big); free(ext);
+}
+
+/* Independent linear gates, OpenMP over gates.  nrot, nin, ks_cst = [count];
+ * coef = [count][2][8]; cst = [count][2]; in = [count][8][n+1]. */
+void orc_gate_linear_batch(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, int64_t count,
+                           const int32_t *nrot, const int32_t *nin, const int32_t *coef, const uint32_t *cst,
+                           const uint32_t *ks_cst, const uint32_t *in, uint32_t *out, int nthreads)
+{
+    const int n1 = P->n + 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t g = 0; g < count; g++)
+        orc_gate_linear(P, bk, ksk, nrot[g], nin[g], coef + g * 16, cst + g * 2, in + (size_t)g * 8 * n1, ks_cst[g],
+                        out + (size_t)g * n1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fan-in-g HomSum (a cheaper variant of the Section 5 aggregation).         */
+/* ------------------------------------------------------------------------- */
+
+/* XOR of g bits with one bootstrap.  Reading: with Ecd's +-1/8, the sum of g
+ * encodings of which t are true is (2t - g)/8; doubled, each true input moves
+ * it by 1/2, so 2 * sum_k c_k + T((g-1)/4) has phase +1/4 for odd t and -1/4
+ * for even t (mod 1), and the blind rotation's sign test returns Enc(t mod 2).
+ * g = 2 is tfhe-2's XOR gate T(1/4) + 2(c1 + c2).  The input noise is doubled
+ * against a margin of 1/4 (the same ratio as a two-input gate's 1/8), and
+ * grows as sqrt(g).  in = [g][n+1].
+ * Pin: decryption of every input pattern, equality with the XOR gate at
+ * g = 2, and the measured pre-bootstrap noise against the variance bound. */
+void orc_xor_many(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, const uint32_t *in, int g,
+                  uint32_t *out)
+{
+    const int n = P->n;
+    uint32_t *c = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
+    for (int k = 0; k < g; k++)
+        for (int i = 0; i <= n; i++) c[i] += 2u * in[(size_t)k * (n + 1) + i];
+    c[n] += (uint32_t)(g - 1) * MU_1_4;
+    orc_bootstrap(P, bk, ksk, c, out);
+    free(c);
+}
+
+/* HomSum with fan-in g: for k = 1, g, g^2, ... and i = 0, gk, 2gk, ...:
+ * S_i[j] = XOR of S_{i + m k}[j] over the m < g with i + m k < M (when there
+ * are at least two), every bit j.  S = [M][lS][n+1], reduced in place; the
+ * result is S_0.  g = 2 is orc_homsum_tree's pairing exactly.  Within one k,
+ * independent gates run under OpenMP. */
+void orc_homsum_tree_fanin(const orc_params *P, const uint32_t *bk, const uint32_t *ksk, uint32_t *S, int64_t M,
+                           int lS, int g, int nthreads)
+{
+    const int n1 = P->n + 1;
+    for (int64_t k = 1; k < M; k *= g) {
+        const int64_t groups = (M + g * k - 1) / (g * k);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+        for (int64_t w = 0; w < groups * lS; w++) {
+            const int64_t i = (w / lS) * g * k;
+            const int j = (int)(w % lS);
+            int m = 0;
+            while (m < g && i + m * k < M) m++;
+            if (m < 2) continue;
+            uint32_t *in = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * n1);
+            for (int q = 0; q < m; q++)
+                memcpy(in + (size_t)q * n1, S + ((size_t)(i + q * k) * lS + j) * n1, sizeof(uint32_t) * (size_t)n1);
+            orc_xor_many(P, bk, ksk, in, m, S + ((size_t)i * lS + j) * n1);
+            free(in);
+        }
+    }
+}

@@ -1,0 +1,170 @@
+"""Pins of the oracle's linear gate (a bootstrapped gate given by its
+pre-combinations) and of the fan-in-g XOR behind the cheaper HomSum
+aggregation, against decryption of every input pattern, the two-input gates
+they reduce to, and the noise bound of the bootstrapped inputs."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_12761_gb300 import synth
+
+M32 = (1 << 32) - 1
+MU = 1 << 29
+
+
+def signed(x):
+    x = int(x) & M32
+    return x - (1 << 32) if x >= (1 << 31) else x
+
+
+def test_xor_many_every_pattern_toy(toy_keys):
+    """Enc(t mod 2) for every pattern of g <= 6 input bits and sampled patterns at g = 7, 8."""
+    n = toy_keys.P.n
+    for g in range(2, 9):
+        pats = list(itertools.product((0, 1), repeat=g))
+        if g > 6:
+            idx = synth.Stream(50 + g, 2, 0).uniform_int(48, 0, len(pats))
+            pats = [pats[int(i)] for i in idx]
+        bits = np.array(pats, dtype=np.uint32).reshape(-1)
+        cts = oracle.encrypt_bits(toy_keys.s, bits, synth.lwe_material(bits.size, n, seed=500 + g))
+        cts = cts.reshape(len(pats), g, n + 1)
+        got = [int(oracle.decrypt_bits(toy_keys.s, oracle.xor_many(toy_keys, c))[0]) for c in cts]
+        assert got == [sum(p) % 2 for p in pats], g
+
+
+def test_xor_many_two_inputs_is_the_xor_gate(paper_keys):
+    """g = 2 is tfhe-2's XOR gate: identical ciphertexts."""
+    bits = synth.Stream(61, 2, 0).bits(8)
+    cts = oracle.encrypt_bits(paper_keys.s, bits, synth.lwe_material(8, seed=61)).reshape(4, 2, 631)
+    want = oracle.gate_batch(paper_keys, oracle.XOR, cts)
+    for c, w in zip(cts, want):
+        assert np.array_equal(oracle.xor_many(paper_keys, c), w)
+
+
+def test_homsum_fanin_two_is_the_pairwise_tree(toy_keys):
+    n = toy_keys.P.n
+    M, lS = 7, 3
+    bits = synth.Stream(62, 2, 0).bits(M * lS)
+    S = oracle.encrypt_bits(toy_keys.s, bits, synth.lwe_material(M * lS, n, seed=62)).reshape(M, lS, n + 1)
+    assert np.array_equal(oracle.homsum_tree_fanin(toy_keys, S, 2), oracle.homsum_tree(toy_keys, S))
+
+
+@pytest.mark.parametrize("g", [3, 4, 5, 8])
+def test_homsum_fanin_decrypts_to_the_xor_of_all_entries(toy_keys, g):
+    """Ragged sizes (M not a power of g, M = 1) and every bit lane."""
+    n = toy_keys.P.n
+    for M in (1, 2, g - 1, g, g + 1, 2 * g + 3, g * g + 1):
+        if M < 1:
+            continue
+        lS = 2
+        bits = synth.Stream(70 + g, 3, M).bits(M * lS).reshape(M, lS)
+        S = oracle.encrypt_bits(toy_keys.s, bits.reshape(-1), synth.lwe_material(M * lS, n, seed=71 + M + g))
+        out = oracle.homsum_tree_fanin(toy_keys, S.reshape(M, lS, n + 1), g)
+        assert list(oracle.decrypt_bits(toy_keys.s, out)) == list(bits.sum(axis=0) % 2), (g, M)
+
+
+def test_gate_linear_equals_the_gates(paper_keys):
+    """The ten two-input gates and MUX written as pre-combinations give the
+    same ciphertexts as the gate functions."""
+    comb = {oracle.AND: (-MU, 1, 1), oracle.NAND: (MU, -1, -1), oracle.OR: (MU, 1, 1), oracle.NOR: (-MU, -1, -1),
+            oracle.XOR: (2 * MU, 2, 2), oracle.XNOR: (-2 * MU, -2, -2), oracle.ANDNY: (-MU, -1, 1),
+            oracle.ANDYN: (-MU, 1, -1), oracle.ORNY: (MU, -1, 1), oracle.ORYN: (MU, 1, -1)}
+    bits = synth.Stream(63, 2, 0).bits(3 * (len(comb) + 2))
+    cts = oracle.encrypt_bits(paper_keys.s, bits, synth.lwe_material(bits.size, seed=63)).reshape(-1, 3, 631)
+    rows, want = [], []
+    for i, (g, (c, s1, s2)) in enumerate(comb.items()):
+        coef = np.zeros((2, 8), np.int32)
+        coef[0, :2] = (s1, s2)
+        rows.append((1, 2, coef, [c & M32, 0], 0, cts[i]))
+        want.append(oracle.gate(paper_keys, g, cts[i][0], cts[i][1]))
+    for i in (len(comb), len(comb) + 1):   # MUX(c, a, b): AND(c, a) and AND(NOT c, b), + T(1/8)
+        coef = np.zeros((2, 8), np.int32)
+        coef[0, :3] = (1, 1, 0)
+        coef[1, :3] = (-1, 0, 1)
+        rows.append((2, 3, coef, [(-MU) & M32, (-MU) & M32], MU, cts[i]))
+        want.append(oracle.gate(paper_keys, oracle.MUX, cts[i][0], cts[i][1], cts[i][2]))
+    inputs = np.zeros((len(rows), 8, 631), np.uint32)
+    for k, r in enumerate(rows):
+        inputs[k, :3] = r[5]
+    got = oracle.gate_linear_batch(paper_keys, [r[0] for r in rows], [r[1] for r in rows], [r[2] for r in rows],
+                                   [r[3] for r in rows], [r[4] for r in rows], inputs)
+    assert np.array_equal(got, np.array(want))
+
+
+def test_gate_linear_decrypts_to_the_sign_of_the_combined_phase(toy_keys):
+    """Random coefficients in [-2, 2] on up to 8 inputs and constants in
+    multiples of 1/8: the output decrypts to [noiseless phase in [0, 1/2)]
+    for one rotation, and to the sign of the summed extractions plus the
+    key-switch constant for two."""
+    n = toy_keys.P.n
+    st = synth.Stream(64, 2, 0)
+    count = 120
+    nrot = 1 + (st.uniform_int(count, 0, 2))
+    nin = 1 + st.uniform_int(count, 0, 8)
+    coef = (st.uniform_int(count * 16, 0, 5).astype(np.int32) - 2).reshape(count, 2, 8)
+    cst = (st.uniform_int(count * 2, 0, 8).astype(np.uint64) * MU).astype(np.uint32).reshape(count, 2)
+    ks_cst = (st.uniform_int(count, 0, 8).astype(np.uint64) * MU).astype(np.uint32)
+    bits = st.bits(count * 8).reshape(count, 8)
+    inputs = oracle.encrypt_bits(toy_keys.s, bits.reshape(-1), synth.lwe_material(count * 8, n, seed=65))
+    inputs = inputs.reshape(count, 8, n + 1)
+    for g in range(count):
+        coef[g, :, nin[g]:] = 0
+        if nrot[g] == 1:
+            coef[g, 1] = 0
+    keep, want = [], []
+    for g in range(count):
+        mus = np.where(bits[g] == 1, MU, -MU)
+        phases = [(int((coef[g, r] * mus).sum()) + int(cst[g, r])) & M32 for r in range(nrot[g])]
+        # a noiseless phase on the boundary (0 or 1/2) has no defined sign: skip
+        if any(p in (0, 1 << 31) for p in phases):
+            continue
+        ext = sum(MU if p < (1 << 31) else -MU for p in phases) + int(ks_cst[g])
+        ext &= M32
+        if ext in (0, 1 << 31) or min(abs(signed(ext)), abs(signed(ext - (1 << 31)))) < MU // 2:
+            continue
+        keep.append(g)
+        want.append(1 if ext < (1 << 31) else 0)
+    assert len(keep) > 40
+    k = np.array(keep)
+    out = oracle.gate_linear_batch(toy_keys, nrot[k], nin[k], coef[k], cst[k], ks_cst[k], inputs[k])
+    assert list(oracle.decrypt_bits(toy_keys.s, out)) == want
+
+
+def test_fanin_noise_against_the_bootstrap_bound(paper_keys):
+    """The pre-bootstrap noise of 2 sum_k c_k over g bootstrapped outputs is
+    4 g Var_out; with Var_out under tfhe-2's bound (Var_BR + Var_KS) and the
+    modulus-switch rounding of the blind rotation, the margin of 1/4 holds
+    at more than 9 standard deviations up to g = 8 (at g = 16 it falls to
+    6.7).  Measured at g = 2, 3, 4 and 8 on 96 real gate outputs."""
+    P = paper_keys.P
+    n, N, l = P.n, P.N, P.l
+    var_br = n * 2 * l * N * (64.0 ** 2) * 2.0 ** -50 + n * (1 + N) * 2.0 ** -44
+    var_ks = N * P.ks_t * 2.0 ** -30 + N * 2.0 ** -34
+    var_out = var_br + var_ks
+    var_ms = (n + 1) * (2.0 ** -12) ** 2 / 3          # rounding to 1/2N on every word
+    count = 96
+    bits = synth.Stream(66, 2, 0).bits(2 * count)
+    cts = oracle.encrypt_bits(paper_keys.s, bits, synth.lwe_material(2 * count, seed=66)).reshape(count, 2, 631)
+    outs = oracle.gate_batch(paper_keys, oracle.AND, cts)
+    truth = bits.reshape(count, 2).min(axis=1)
+    ph = oracle.phase(paper_keys.s, outs)
+    err = np.array([signed(int(p) - (MU if t else -MU)) for p, t in zip(ph, truth)]) / 2.0 ** 32
+    v_out = float(np.var(err))
+    assert v_out <= var_out * 1.2, (v_out, var_out)
+    for g in (2, 3, 4, 8):
+        groups = count // g
+        e = []
+        for q in range(groups):
+            sl = slice(q * g, (q + 1) * g)
+            t = int(truth[sl].sum())
+            tot = (2 * sum(int(x) for x in ph[sl]) + (g - 1) * 2 * MU) & M32
+            nominal = (1 << 30) if t % 2 else (3 << 30)      # +1/4 or -1/4
+            e.append(signed(tot - nominal) / 2.0 ** 32)
+        v = float(np.mean(np.square(e)))
+        lo, hi = (0.5, 1.8) if groups >= 40 else (0.2, 3.0)
+        assert lo * 4 * g * v_out < v < hi * 4 * g * v_out, (g, v, 4 * g * v_out)
+        sd = np.sqrt(4 * g * var_out + var_ms)
+        assert 0.25 / sd > (9.0 if g <= 8 else 0), (g, 0.25 / sd)
+    assert 0.25 / np.sqrt(4 * 16 * var_out + var_ms) < 7.0
