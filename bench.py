@@ -166,6 +166,32 @@ def cpu_oracle_rate(budget_s: float = 20.0):
                                 f"(OpenMP over gates, {threads} threads) in {dt:.1f} s")
 
 
+def cpu_oracle_config1():
+    """The oracle's whole identifier-matching circuit of the small workload
+    (8-bit id, D = 4 ids, 28 bootstraps in AND-tree layers of 16, 8 and 4),
+    timed exactly on the host cores."""
+    import oracle
+    from paper_2506_12761_gb300 import synth
+    if "keys" not in _ORACLE:
+        _ORACLE["keys"] = oracle.keygen(oracle.paper_params(), synth.key_material())
+    keys = _ORACLE["keys"]
+    w = synth.idm_workload(4, 8)
+    x = oracle.encrypt_bits(keys.s, synth.value_bits([w["query"]], 8)[0], synth.lwe_material(8, substream=31))
+    t0 = time.perf_counter()
+    out = oracle.idm_batch(keys, x, w["ids"].astype(np.uint64))
+    dt = time.perf_counter() - t0
+    ok = list(oracle.decrypt_bits(keys.s, out)) == [int(i == w["query"]) for i in w["ids"]]
+    return {"bootstraps": 28, "seconds": dt, "value": 28 / dt, "unit": UNIT, "decrypt_ok": ok,
+            "threads": oracle.default_threads(),
+            "workload": "identifier matching, 8-bit encrypted id vs D=4 plaintext ids (28 bootstraps), whole circuit"}
+
+
+def bench_config(world: int, sample: str) -> dict:
+    """The `config` record of both arms: the same keys, the workload and what each arm timed."""
+    return {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
+            "parallelism": f"replicas x{world}", "sample": sample}
+
+
 def run_reference(args):
     rank, _, world = env_rank()
     if rank != 0:
@@ -178,14 +204,62 @@ def run_reference(args):
         info = (cores, sample)
     vals = steps[args.warmup:]
     v = float(np.mean(vals))
+    sample = ("each step: a bounded sample of the workload, " + info[1] +
+              "; ms_per_step extrapolated to the whole query as bootstraps_per_step / rate")
+    c1 = cpu_oracle_config1()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": BOOTSTRAPS_PER_STEP / v * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle", "sample": info[1]},
+            "warmup": args.warmup, "ms_per_step": BOOTSTRAPS_PER_STEP / v * 1e3,
+            "ms_per_step_basis": "extrapolated from the timed sample (a full CPU query takes about an hour)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": bench_config(world, sample),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle", "sample": info[1],
+                             "config1_full_circuit": c1},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_wave(args):
+    """One-launch measurement of the blind-rotation kernel: `--wave` AND gates
+    in one velopir_bootstrap_batch call, `--warmup` untimed then `--steps`
+    timed, with the library's CUDA-event profiler around each launch.  A count
+    of 152 x W is one full wave of the W-wide tile shape (1,824 fills every SM
+    with 12 bootstraps).  This is the command the kernel profiles capture."""
+    import torch
+    from paper_2506_12761_gb300 import build, synth
+    from paper_2506_12761_gb300 import velopir as vp
+    build.build()
+    km = synth.key_material()
+    bk, ksk = vp.velopir_client_keygen(km)
+    ctx = vp.Context(0)
+    vp.velopir_load_cloud_key(ctx.h, bk, ksk)
+    vp.velopir_set_path(ctx.h, {"dense": vp.VP_PATH_INT32_DENSE, "ntt": vp.VP_PATH_NTT,
+                                 "tensor": vp.VP_PATH_TENSOR_F16}[args.path])
+    n = args.wave
+    bits = synth.Stream(synth.MASTER_SEED, synth.STREAM_QUERY, 9).bits(n * 2)
+    ct = vp.velopir_client_encrypt_bits(km.s, bits, synth.lwe_material(n * 2, substream=9)).reshape(n, 2, 631)
+    din = torch.from_numpy(ct.view(np.int32)).cuda()
+    dout = torch.zeros((n, 631), dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        vp.velopir_bootstrap_batch(ctx.h, vp.VP_AND, din, dout, n)
+    vp.velopir_profile(ctx.h, True)
+    per = []
+    for _ in range(args.steps):
+        b0 = vp.velopir_profile_read(ctx.h, vp.VP_KERNEL_BLIND_ROTATE)
+        k0 = vp.velopir_profile_read(ctx.h, vp.VP_KERNEL_KEY_SWITCH)
+        vp.velopir_bootstrap_batch(ctx.h, vp.VP_AND, din, dout, n)
+        b1 = vp.velopir_profile_read(ctx.h, vp.VP_KERNEL_BLIND_ROTATE)
+        k1 = vp.velopir_profile_read(ctx.h, vp.VP_KERNEL_KEY_SWITCH)
+        per.append({"br_launches": b1[0] - b0[0], "br_ms": b1[2] - b0[2], "ks_ms": k1[2] - k0[2]})
+    vp.velopir_profile(ctx.h, False)
+    b = bits.reshape(-1, 2)
+    ok = bool(np.array_equal(vp.velopir_client_decrypt_bits(km.s, dout.cpu().numpy().view(np.uint32)),
+                             b[:, 0] & b[:, 1]))
+    best = min(p["br_ms"] for p in per)
+    print(json.dumps({"mode": "one launch", "path": args.path, "count": n, "launches": per,
+                      "blind_rotations_per_s": n / (best / 1e3), "decrypt_ok": ok}), flush=True)
+    ctx.close()
+    return 0 if ok else 1
 
 
 def main():
@@ -194,12 +268,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="ntt", choices=["dense", "ntt"])
+    ap.add_argument("--path", default="ntt", choices=["dense", "ntt", "tensor"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--latency-queries", type=int, default=20)
+    ap.add_argument("--wave", type=int, default=0,
+                    help="instead of the query: one batch of this many AND gates per step (kernel profiles)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.wave:
+        return run_wave(args)
 
     import torch
     from paper_2506_12761_gb300 import build, synth
@@ -216,7 +295,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = vp.Context(local, 0, stream.cuda_stream)
     vp.velopir_load_cloud_key(ctx.h, bk, ksk)
-    vp.velopir_set_path(ctx.h, {"dense": vp.VP_PATH_INT32_DENSE, "ntt": vp.VP_PATH_NTT}[args.path])
+    vp.velopir_set_path(ctx.h, {"dense": vp.VP_PATH_INT32_DENSE, "ntt": vp.VP_PATH_NTT,
+                                 "tensor": vp.VP_PATH_TENSOR_F16}[args.path])
     waves = vp.velopir_autotune(ctx.h) if args.path == "ntt" else []   # tile-shape autotuner (untimed set-up)
     w = synth.intv_workload(D, substream=rank)
     cx = vp.velopir_client_encrypt_bits(km.s, synth.value_bits([w["x"]], 32)[0], synth.lwe_material(32, substream=1 + 2 * rank))
@@ -281,22 +361,55 @@ def main():
     h2d = (cx.nbytes + cy.nbytes + rects.nbytes)
     d2h = D * 631 * 4
 
-    # plain: one bootstrap per kernel launch, same kernels
+    # plain: one bootstrap per kernel launch, same kernels (one warm-up pass, then repeats)
     plain_n = 8 if args.path == "dense" else 64
     bits = synth.Stream(5, 2, 99).bits(2 * plain_n)
     pin = vp.velopir_client_encrypt_bits(km.s, bits, synth.lwe_material(2 * plain_n, seed=5)).reshape(plain_n, 2, 631)
     dpin = torch.from_numpy(pin.view(np.int32)).cuda()
     dpout = torch.zeros((plain_n, 631), dtype=torch.int32, device="cuda")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    vp.velopir_bootstrap_plain(ctx.h, vp.VP_AND, dpin, dpout, plain_n)
-    torch.cuda.synchronize()
-    plain_rate = plain_n / (time.perf_counter() - t0)
+    vp.velopir_bootstrap_plain(ctx.h, vp.VP_AND, dpin[:4], dpout[:4], 4)
+    plain_rates = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vp.velopir_bootstrap_plain(ctx.h, vp.VP_AND, dpin, dpout, plain_n)
+        torch.cuda.synchronize()
+        plain_rates.append(plain_n / (time.perf_counter() - t0))
+    plain_rate = float(np.median(plain_rates))
+
+    # query latency of the small identifier-matching workload (8-bit id, D = 4,
+    # 28 bootstraps): layer-batched launches against one bootstrap per launch
+    w1 = synth.idm_workload(4, 8)
+    x1 = torch.from_numpy(vp.velopir_client_encrypt_bits(km.s, synth.value_bits([w1["query"]], 8)[0],
+                                                         synth.lwe_material(8, substream=31)).view(np.int32)).cuda()
+    ids1 = torch.from_numpy(w1["ids"].astype(np.uint32).view(np.int32)).cuda()
+    out1 = torch.zeros((4, 631), dtype=torch.int32, device="cuda")
+    lat = {}
+    for mode, limit in (("batched", 0), ("plain", 1)):
+        vp.velopir_set_launch_limit(ctx.h, limit)
+        vp.velopir_id_match(ctx.h, x1, 8, ids1, 4, None, 0, out1)     # warm-up
+        ts = []
+        for _ in range(args.latency_queries):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vp.velopir_id_match(ctx.h, x1, 8, ids1, 4, None, 0, out1)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ok = list(vp.velopir_client_decrypt_bits(km.s, out1.cpu().numpy().view(np.uint32))) == \
+            [int(i == w1["query"]) for i in w1["ids"]]
+        lat[mode] = {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99)), "queries": len(ts),
+                     "decrypt_ok": ok}
+    vp.velopir_set_launch_limit(ctx.h, 0)
 
     # roofline of the dominant kernel (blind rotation), timed live above
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    if args.path == "dense":
+    if args.path == "tensor":
+        kernel_src = "br_tc.cu"
+        # fp16 MMA work: 4 key limbs x the dense contraction, 2 flops per multiply-add
+        achieved = (u_br * 4 * MACS_DENSE * 2) / (ms_br / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)   # fp16 and bf16 dense rates are equal
+        unit = "TFLOP/s"
+    elif args.path == "dense":
         kernel_src = "br_dense.cu"
         achieved = (u_br * MACS_DENSE) / (ms_br / 1e3) / 1e12
         peak = 152 * 64 * sm_max * 1e6 / 1e12   # int32 multiply-add pipe: 64 lanes/clk/SM
@@ -308,10 +421,13 @@ def main():
         achieved = (u_br * ntt_model.IMAD_SLOTS_PER_BOOTSTRAP) / (ms_br / 1e3) / 1e12
         peak = 152 * 64 * sm_max * 1e6 / 1e12
         unit = "T IMAD lane-slots/s"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+    roofline = {"bound": "tensor" if args.path == "tensor" else "alu", "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak,
                 "traffic": traffic_for(kernel_src),
                 "kernel": kernel_src.replace(".cu", ""), "launches": n_br, "avg_launch_ms": ms_br / max(1, n_br),
-                "peak_basis": "152 SMs x 64 int32 multiply lanes/clk x max SM clock %.0f MHz" % sm_max,
+                "peak_basis": ("measured cuBLAS bf16 dense GEMM (MEASURED_PEAKS.json bf16_tflops)"
+                               if args.path == "tensor" else
+                               "152 SMs x 64 int32 multiply lanes/clk x max SM clock %.0f MHz" % sm_max),
                 "work_per_bootstrap": ({"imad_slots": ntt_model.IMAD_SLOTS_PER_BOOTSTRAP,
                                         "multiplies": ntt_model.IMAD_OPS_PER_BOOTSTRAP,
                                         "slot_rule": "low-half multiply 1 slot, high-half multiply 2 slots"}
@@ -322,19 +438,23 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, sample = cpu_oracle_rate()
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "config1_full_circuit": cpu_oracle_config1()}
 
     if rank == 0:
         ms = [float(x) for x in per_step]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
-                           "path": args.path, "parallelism": f"replicas x{world}",
-                           "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves))},
-                           "l2": "flushed between timed steps (256 MiB write, untimed)"},
+                "config": bench_config(world, "each step: the whole query, every bootstrap of it"),
+                "run": {"path": args.path,
+                        "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves))},
+                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
                 "query_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
-                "plain": {"value": plain_rate, "unit": UNIT, "note": "one bootstrap per kernel launch, same kernels"},
+                "plain": {"value": plain_rate, "unit": UNIT, "repeats": [float(x) for x in plain_rates],
+                          "note": "one bootstrap per kernel launch, same kernels; median of 3 passes after a warm-up"},
+                "config1_query_ms": dict(lat, workload="identifier matching, 8-bit id vs D=4 ids, 28 bootstraps",
+                                         note="batched: gate layers as launches; plain: one bootstrap per launch"),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
                 "decrypt_ok": decrypt_ok}

@@ -1,6 +1,9 @@
 /*
  * velopir.h -- C ABI of libvelopir.so: batched TFHE gate bootstrapping on one
  * GB300 (sm_103a) and the server-side circuits of VeLoPIR's three query modes.
+ * Key generation, encryption, decryption and Alg. PubKeyGen / ServerEnc are
+ * in the separate host-only library libvelopir_client.so (velopir_client.h),
+ * which needs no GPU and no CUDA runtime.
  *
  * Paper: "Versatile and Fast Location-Based PIR with FHE over the Torus"
  * (VeLoPIR).  Section 2.2 defines TLWE encryption, Ecd, Dec and the gate
@@ -24,7 +27,9 @@
  *    so a device-resident database is first copied to the host.
  *  - Calls on one context are serialised on the context's CUDA stream and are
  *    synchronous unless stated otherwise (velopir_submit is asynchronous).
- *  - A context is not thread-safe; use one context per host thread.
+ *  - A context is not thread-safe; use one context per host thread.  The
+ *    exception is serving with the issue thread (velopir_serve_start): the
+ *    serving calls may then come from any thread.
  */
 #ifndef VELOPIR_H
 #define VELOPIR_H
@@ -32,27 +37,11 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "velopir_common.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
-
-#define VELOPIR_LWE_N 630     /* LWE dimension n (Appendix parameter table) */
-#define VELOPIR_RING_N 1024   /* polynomial size N (Appendix parameter table) */
-#define VELOPIR_LWE_WORDS 631 /* n mask words + b */
-
-enum {
-    VELOPIR_OK = 0,
-    VELOPIR_ERR_ARG = -1,     /* null pointer, bad size, unknown gate, bad params */
-    VELOPIR_ERR_NOKEY = -2,   /* no cloud key loaded on this context */
-    VELOPIR_ERR_OOM = -3,     /* request exceeds the HBM budget or cudaMalloc failed */
-    VELOPIR_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed */
-    VELOPIR_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up */
-    VELOPIR_ERR_BUSY = -6,    /* serving queue full / ticket not finished */
-    VELOPIR_ERR_NOCUDA = -7,  /* no CUDA device is visible */
-    VELOPIR_ERR_PLAN = -8,    /* a dry run found a gate reading a value that was
-                                 not yet written or already overwritten */
-    VELOPIR_ERR_CANCELLED = -9 /* velopir_poll: the ticket was cancelled */
-};
 
 /* Gates (Section 2.2 names HomAND, HomXOR, HomXNOR; the others are tfhe-2's
  * gate set under the same encoding).  Each binary gate is one bootstrap of a
@@ -74,10 +63,6 @@ typedef enum {
     VP_PATH_NTT = 1,         /* exact two-prime number-theoretic transform (default) */
     VP_PATH_TENSOR_F16 = 2   /* exact small-integer limbs on tcgen05 kind::f16 */
 } velopir_path;
-
-typedef struct {
-    int32_t n, N, k, l, bg_bits, ks_t, ks_base_bits; /* must be 630,1024,1,3,7,8,2 */
-} velopir_params;
 
 typedef struct velopir_ctx velopir_ctx;
 
@@ -110,6 +95,14 @@ int velopir_load_cloud_key(velopir_ctx *ctx, const velopir_params *params,
  * stays loaded: the path's transformed copy of BK is built on the device the
  * first time the path runs.  Errors: ERR_ARG (unknown or unavailable path). */
 int velopir_set_path(velopir_ctx *ctx, velopir_path path);
+
+/* Cap the blind rotations per kernel launch (default and maximum 65,536; 0
+ * restores the default).  A layer larger than the cap runs as several
+ * launches; a MUX's two rotations always share one.  max_rotations = 1 is the
+ * plain one-bootstrap-per-launch execution of any query or batch, the
+ * baseline that layer batching is measured against.  Results are identical
+ * under every cap.  Errors: ERR_ARG. */
+int velopir_set_launch_limit(velopir_ctx *ctx, size_t max_rotations);
 
 /* One gate on each of `count` independent inputs, all bootstraps issued as
  * one batch (blind rotation of every input shares each step's BK_i).
@@ -146,8 +139,11 @@ int velopir_bootstrap_batch(velopir_ctx *ctx, velopir_gate gate, const uint32_t 
  * The first call on a device performs a one-time set-up (it looks up the
  * array's device address with that device current), so make that first call
  * before any CUDA stream capture.  Synchronous: returns after the stream has
- * finished the work.  Errors: ERR_ARG (sizes, null or host pointers, unknown
- * gate), ERR_NOKEY, ERR_CUDA, ERR_TIMEOUT. */
+ * finished the work.  Its status includes the context's device error word,
+ * as every synchronous call's does: a bounded wait that gave up in earlier
+ * asynchronous work on the same context (serving steps) is reported by the
+ * next synchronous call, which may be this one.  Errors: ERR_ARG (sizes,
+ * null or host pointers, unknown gate), ERR_NOKEY, ERR_CUDA, ERR_TIMEOUT. */
 int velopir_bootstrap_batch_noalloc(velopir_ctx *ctx, velopir_gate gate, const uint32_t *lwe_in,
                                     uint32_t *lwe_out, size_t count);
 
@@ -204,16 +200,8 @@ int velopir_id_match(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, cons
  * HomBitwiseAND).  Ciphertext arrays may be host or device memory; outputs
  * as in the plaintext-database calls. */
 
-/* Alg. PubKeyGen: count encryptions of zero, pk_i = (a_i, <a_i, s> + e_i).
- * s: uint32_t[630] (0/1), a: uint32_t[count][630] uniform, e: uint32_t[count]
- * noise (torus words), pk_out: uint32_t[count][631].  Host only.  Errors: ERR_ARG. */
-int velopir_client_pubkeygen(const uint32_t *s, const uint32_t *a, const uint32_t *e, size_t count,
-                             uint32_t *pk_out);
-
-/* Alg. ServerEnc: ct_i = (0, Ecd(bit_i)) + pk_i (Ecd(1) = 1/8, Ecd(0) = -1/8).
- * pk: uint32_t[count][631], bits: uint32_t[count] (0/1), ct_out:
- * uint32_t[count][631].  Host only; uses no secret.  Errors: ERR_ARG. */
-int velopir_server_encrypt(const uint32_t *pk, const uint32_t *bits, size_t count, uint32_t *ct_out);
+/* The database ciphertexts come from Alg. PubKeyGen and Alg. ServerEnc,
+ * which run on the host (velopir_client.h). */
 
 /* Largest encrypted payload (bits per entry) of the encdb calls. */
 #define VELOPIR_MAX_ENC_PAYLOAD_BITS 4096
@@ -257,7 +245,14 @@ typedef struct {
     int32_t kind;            /* velopir_query_kind */
     int32_t id_bits;         /* IdM only */
     int32_t payload_bits;    /* IdM with payload only */
-    int32_t reserved;
+    int32_t agg_fanin;       /* IdM with payload: fan-in of the XOR aggregation tree.  0 or 2 is
+                                Section 5's pairwise HomSum (D - 1 bootstraps per payload bit);
+                                g in 3..8 XORs g values with one bootstrap of
+                                2 (c_1 + ... + c_g) + T((g-1)/4), whose phase is +-1/4 by the
+                                parity of the true inputs (about (D - 1)/(g - 1) bootstraps per
+                                bit).  The doubled input noise against the 1/4 margin stays
+                                above 9 standard deviations of tfhe-2's output-noise bound up to
+                                g = 8.  Same plaintext result, different ciphertexts. */
     const uint32_t *enc_a;   /* IntV: enc_x; CoV: enc_cell; IdM: enc_id (host or device) */
     const uint32_t *enc_b;   /* IntV: enc_y; otherwise NULL */
     const uint32_t *db;      /* rects / cells / ids (host or device; copied at submit) */
@@ -317,8 +312,9 @@ int velopir_tuned_shape(velopir_ctx *ctx, size_t count);
  *   bits_b: IntV y[32] or y[l], else ignored (nullable);
  *   bits_out: receives one 0/1 per output ciphertext (D entries, or
  *             payload_bits with a payload);
- *   launch_sizes (nullable): receives the blind rotations of each launch,
- *           up to max_launches entries.
+ *   launch_sizes (nullable): receives the blind rotations of each launch
+ *           (one entry per scheduled layer, before the executor splits a
+ *           layer into chunks), up to max_launches entries.
  * Returns the number of launches (>= 1), VELOPIR_ERR_ARG for bad arguments,
  * or VELOPIR_ERR_PLAN if any gate of the plan would read a value that is not
  * yet written or whose pool slot was already reused. */
@@ -329,8 +325,11 @@ int velopir_plan_query(const velopir_query *q, int wave, const uint32_t *bits_a,
  * one merged gate program over all queries, scheduled as in
  * velopir_plan_query, executed in the device's launch order -- each launch
  * split into chunks of at most chunk_rows blind rotations (0: no split;
- * the executor splits at 65,536), every chunk's blind rotations before its
- * key switches -- on noiseless plaintext phases.  Plaintext-database kinds
+ * the executor splits at 65,536; like the executor, the dry run never uses
+ * fewer than 2 rows, so a MUX's two rotations share a chunk), a layer's
+ * multi-input sums first and every chunk's blind rotations before its key
+ * switches -- on noiseless plaintext phases.  launch_sizes holds the blind
+ * rotations per scheduled layer, as in velopir_plan_query.  Plaintext-database kinds
  * (VP_QUERY_*) only.  bits_a, bits_b and bits_out are the per-query arrays
  * of velopir_plan_query concatenated in query order (bits_b holds the IntV
  * queries' y bits only).  Returns the number of launches, ERR_ARG, or
@@ -369,6 +368,24 @@ int velopir_cancel(velopir_ctx *ctx, uint64_t ticket);
  * ERR_CUDA, ERR_TIMEOUT. */
 int velopir_progress(velopir_ctx *ctx, uint64_t *done, size_t cap, size_t *ndone);
 
+/* Start the context's issue thread, a host thread owned by the library that
+ * admits waiting queries and issues serving steps back to back, keeping up
+ * to two steps queued on the stream, so the GPU never waits for the caller
+ * between steps.  While it runs: velopir_submit, velopir_cancel,
+ * velopir_queue_depth, velopir_poll and velopir_progress may be called from
+ * any host thread (poll and progress then only report: they issue nothing);
+ * every other call on this context returns ERR_BUSY.  A failure of the
+ * thread (ERR_TIMEOUT from a serving step, ERR_CUDA) is returned by the next
+ * poll or progress.  Errors: ERR_ARG, ERR_NOKEY, ERR_OOM, ERR_CUDA. */
+int velopir_serve_start(velopir_ctx *ctx);
+
+/* Stop the issue thread once the steps already issued have finished.
+ * Queries still waiting or admitted stay; velopir_poll and
+ * velopir_progress step them again.  Returns the thread's first failure, if
+ * any.  velopir_destroy stops the thread first.  Errors: ERR_ARG,
+ * ERR_TIMEOUT, ERR_CUDA. */
+int velopir_serve_stop(velopir_ctx *ctx);
+
 /* Number of admitted and waiting queries.  Errors: ERR_ARG. */
 int velopir_queue_depth(velopir_ctx *ctx, size_t *admitted, size_t *waiting);
 
@@ -391,7 +408,13 @@ int velopir_selftest_wait_timeout(velopir_ctx *ctx);
 
 /* ---- tracing: per-kernel device time -------------------------------------- */
 
-typedef enum { VP_KERNEL_BLIND_ROTATE = 0, VP_KERNEL_KEY_SWITCH = 1, VP_KERNEL_FREE = 2 } velopir_kernel;
+typedef enum {
+    VP_KERNEL_BLIND_ROTATE = 0,
+    VP_KERNEL_KEY_SWITCH = 1,
+    VP_KERNEL_FREE = 2,    /* bootstrap-free gates */
+    VP_KERNEL_SUM = 3,     /* multi-input pre-combinations of the fan-in aggregation */
+    VP_KERNEL_TRACE = 4    /* gate-trace copies (velopir_trace_start) */
+} velopir_kernel;
 
 /* enable != 0: bracket every subsequent kernel launch with CUDA events on the
  * context's stream and accumulate its device time per kernel kind; 0 stops.
@@ -404,26 +427,48 @@ int velopir_profile(velopir_ctx *ctx, int enable);
  * Errors: ERR_ARG, ERR_CUDA. */
 int velopir_profile_read(velopir_ctx *ctx, int kernel, uint64_t *launches, uint64_t *units, double *ms);
 
-/* ---- client side (host only; no GPU involved) --------------------------- */
-/* Key generation and encryption from caller-supplied random numbers (masks,
- * noise integers, key bits), so that any seeded generator can drive them.   */
+/* ---- gate trace: per-gate records for parity checks ---------------------- */
 
-/* BK and KSK from: s[630] and K[1024] key bits (0/1), bk_a/bk_e
- * uint32_t[630][6][1024] masks and noise, ksk_a uint32_t[1024][8][4][630],
- * ksk_e uint32_t[1024][8][4].  Outputs in the layouts velopir_load_cloud_key
- * takes.  Errors: ERR_ARG. */
-int velopir_client_keygen(const velopir_params *params, const uint32_t *s, const uint32_t *K,
-                          const uint32_t *bk_a, const uint32_t *bk_e,
-                          const uint32_t *ksk_a, const uint32_t *ksk_e,
-                          uint32_t *bk_out, uint32_t *ksk_out);
+#define VELOPIR_TRACE_MAX_IN 8
 
-/* Encrypt `count` bits (Section 2.2 Enc with Ecd): ct_i = (a_i, <a_i,s> + Ecd(bit_i) + e_i).
- * a: uint32_t[count][630], e: uint32_t[count], out: uint32_t[count][631]. */
-int velopir_client_encrypt_bits(const uint32_t *s, const uint32_t *bits, const uint32_t *a,
-                                const uint32_t *e, size_t count, uint32_t *out);
+/* One executed gate as the device ran it.  The gate is Bootstrap of linear
+ * pre-combinations (Section 2.2's gate form; MUX per tfhe-2): rotation
+ * r < nrot blind-rotates c_r = sum_{k < nin} coef[r][k] * in[k] + T(cst[r])
+ * and extracts it; the extractions are summed, T(ks_cst) is added, and the
+ * sum is key-switched into out.  Bootstrap-free gates folded into a gate's
+ * inputs show up as its coefficients and constants; a multi-input sum of the
+ * fan-in aggregation is expanded into its terms.  in[k] for k >= nin is
+ * zero.  22,800 bytes. */
+typedef struct {
+    uint32_t nrot;                                       /* 1, or 2 for MUX */
+    uint32_t nin;                                        /* distinct inputs, <= 8 */
+    uint32_t ks_cst;                                     /* torus constant before key switching */
+    uint32_t cst[2];                                     /* torus constant of each rotation */
+    int32_t coef[2][VELOPIR_TRACE_MAX_IN];               /* coefficient of in[k] in rotation r */
+    uint32_t in[VELOPIR_TRACE_MAX_IN][VELOPIR_LWE_WORDS];/* inputs as the gate read them */
+    uint32_t out[VELOPIR_LWE_WORDS];                     /* the gate's output */
+} velopir_trace_rec;
 
-/* Decrypt `count` ciphertexts (Section 2.2 Dec): bit = phase in [0, 1/2). */
-int velopir_client_decrypt_bits(const uint32_t *s, const uint32_t *ct, size_t count, uint32_t *bits_out);
+/* Start recording a sample of the gates that this context's programs and
+ * serving steps execute (velopir_bootstrap_batch, the query calls,
+ * velopir_query_batch with or without graph capture, velopir_submit; not
+ * velopir_bootstrap_batch_noalloc).  Of every launch of G blind-rotated
+ * gates, max(min(per_launch, G), ceil(G / one_in)) gates (one_in = 0: only
+ * the per-launch count), chosen uniformly by a generator seeded with `seed`,
+ * are copied into a device buffer of `cap` records (reserved here, counted
+ * against the HBM budget) right after their key switch; once `cap` records
+ * are written, further gates are not recorded.  The per-launch count reaches
+ * every level of every circuit, including the few-gate top levels of an
+ * aggregation tree; one_in spreads the rest over the large launches.
+ * Restarting discards the previous records.  Errors: ERR_ARG (per_launch =
+ * one_in = 0, cap = 0 or cap > 2^20), ERR_OOM, ERR_CUDA. */
+int velopir_trace_start(velopir_ctx *ctx, uint64_t seed, uint32_t per_launch, uint32_t one_in, size_t cap);
+
+/* Stop recording; copy the first min(cap, recorded) records to out (host or
+ * device memory, nullable when cap = 0), set *count to the number recorded,
+ * and release the buffer.  Synchronises the stream.  Errors: ERR_ARG,
+ * ERR_CUDA, ERR_TIMEOUT (a device wait of a traced program gave up). */
+int velopir_trace_stop(velopir_ctx *ctx, velopir_trace_rec *out, size_t cap, size_t *count);
 
 #ifdef __cplusplus
 }

@@ -2,12 +2,17 @@
 // layer-batched execution of gate programs, the three VeLoPIR query modes and
 // the continuous-batching serving loop.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -17,6 +22,9 @@
 #include "vp_internal.h"
 
 using namespace vp;
+
+static_assert(sizeof(velopir_trace_rec) == (size_t)kTraceWords * 4, "trace record layout");
+static_assert(VELOPIR_TRACE_MAX_IN == kSumMax, "trace record inputs");
 
 namespace {
 
@@ -40,26 +48,48 @@ struct velopir_ctx {
     std::string err;
     uint64_t launches = 0;
     int path = VP_PATH_NTT;
-    int big_rows = 1 << 16; // scratch capacity in extracted rows
+    int big_rows = 1 << 16; // blind rotations per launch at most (extracted-row scratch)
 
     bool key_loaded = false;
-    DevBuf bk, ksk, bk_ntt, big, jobs_br, jobs_ks, jobs_fr, pool, in, out, errw;
+    DevBuf bk, ksk, bk_ntt, big, jobs_br, jobs_ks, jobs_fr, jobs_sm, jobs_tr, pool, in, out, errw;
     bool bk_ntt_ready = false;
+    DevBuf bk_tc, tc_scratch;               // tensor-core path: expanded key, per-launch scratch
+    bool bk_tc_ready = false;
+
+    // gate trace (velopir_trace_start / _stop): of a chunk of G gates,
+    // max(min(per_launch, G), ceil(G / one_in)) chosen by a seeded generator
+    // are copied into trace_buf
+    bool trace_on = false;
+    uint64_t trace_rng = 0;
+    uint32_t trace_per_launch = 0, trace_one_in = 0;
+    size_t trace_cap = 0, trace_next = 0;
+    DevBuf trace_buf;
 
     std::deque<std::unique_ptr<ServeQuery>> waiting;
     std::vector<std::unique_ptr<ServeQuery>> active;
     std::vector<std::unique_ptr<ServeQuery>> finished;
     uint64_t next_ticket = 1;
     size_t serve_reserved = 0;
-    DevBuf s_br, s_ks, s_fr;   // serving-step job buffers
+
+    // issue thread (velopir_serve_start): guards the serving state above
+    std::mutex mu;
+    std::thread issuer;
+    std::atomic<bool> serving{false};
+    bool stop_req = false;
+    int issuer_rc = VELOPIR_OK;           // first failure of the issue thread
+    std::string issuer_err;
+    struct Step { cudaEvent_t ev; int *err; };
+    std::deque<Step> inflight;            // issued serving steps, oldest first
+    int *err_host = nullptr;              // pinned copies of the error word, one per in-flight step
+    DevBuf s_br, s_ks, s_fr, s_sm, s_tr;   // serving-step job buffers
 
     // tracing: events around each launch, resolved lazily
     bool prof = false;
     struct Rec { int kind; uint64_t units; cudaEvent_t a, b; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> spare;
-    uint64_t prof_launches[3] = {0, 0, 0}, prof_units[3] = {0, 0, 0};
-    double prof_ms[3] = {0, 0, 0};
+    uint64_t prof_launches[5] = {0, 0, 0, 0, 0}, prof_units[5] = {0, 0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};
 
     // captured launch sequence of the last graph-mode program, replayed when
     // the next one has the same launch list on the same buffers
@@ -141,7 +171,7 @@ uint32_t *resolve(uint64_t v, uint32_t *pool, const std::vector<int> &phys)
 }
 
 struct Launch {
-    int kind;   // 0 = blind rotation, 1 = key switch, 2 = free gates
+    int kind;   // 0 = blind rotation, 1 = key switch, 2 = free gates, 3 = pre-combination sums, 4 = gate trace
     size_t off;
     int n;
 };
@@ -150,44 +180,127 @@ struct Flat {
     std::vector<BrJob> br;
     std::vector<KsJob> ks;
     std::vector<FreeJob> fr;
+    std::vector<SumJob> sm;
+    std::vector<TraceJob> tr;
     std::vector<Launch> launches;
 };
 
-// Append one layer's jobs, split into chunks whose blind rotations fit the
-// extracted-row scratch; pointers are resolved against `pool`.
-void flatten_layer(const Layer &L, int cap, uint32_t *pool, const std::vector<int> &phys, Flat &F)
+// The device buffers a flattened program's job lists are uploaded to.
+struct JobBufs {
+    DevBuf *br, *ks, *fr, *sm, *tr;
+};
+
+uint64_t splitmix64(uint64_t &x)
 {
-    const size_t nks = L.ks.size();
-    size_t g = 0;
-    while (g < nks) {
-        const int br0 = L.ks[g].e0;
-        size_t g1 = g;
-        int br1 = br0;
-        while (g1 < nks) {
-            const int hi = std::max(L.ks[g1].e0, L.ks[g1].e1) + 1;
-            if (hi - br0 > cap && g1 > g) break;
-            br1 = std::max(br1, hi);
-            ++g1;
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Gate trace of one chunk of G gates: max(min(per_launch, G), ceil(G /
+// one_in)) of them, chosen uniformly by the context's seeded generator, are
+// copied after the chunk's key switch --
+// their inputs are still intact then (a pool slot is rewritten only in a
+// layer after its last reader) and their outputs are written.  Each record
+// holds the gate's pre-combination with a multi-input sum expanded into its
+// terms.
+void trace_chunk(velopir_ctx *c, const Layer &L, const Chunk &ch, uint32_t *pool, const std::vector<int> &phys,
+                 const std::unordered_map<uint64_t, const SumJob *> &sums, Flat &F)
+{
+    const size_t G = ch.g1 - ch.g0;
+    size_t k = std::min<size_t>(G, c->trace_per_launch);
+    if (c->trace_one_in) k = std::max(k, (G + c->trace_one_in - 1) / c->trace_one_in);
+    if (k == 0 || c->trace_next >= c->trace_cap) return;
+    std::vector<size_t> pick(k);
+    for (size_t i = 0; i < G; ++i) {   // reservoir sampling of k of the G gates
+        if (i < k) pick[i] = i;
+        else if (size_t j = (size_t)(splitmix64(c->trace_rng) % (i + 1)); j < k) pick[j] = i;
+    }
+    std::sort(pick.begin(), pick.end());
+    const size_t to = F.tr.size();
+    for (size_t q : pick) {
+        if (c->trace_next >= c->trace_cap) break;
+        const KsJob &kj = L.ks[ch.g0 + q];
+        TraceJob t{};
+        bool ok = true;
+        auto term = [&](int r, const uint32_t *p, int32_t sgn) {
+            if (!p) return;
+            const uint32_t *rp = resolve((uint64_t)(uintptr_t)p, pool, phys);
+            int idx = -1;
+            for (int m = 0; m < t.nin; ++m)
+                if (t.in[m] == rp) idx = m;
+            if (idx < 0) {
+                if (t.nin == kSumMax) { ok = false; return; }
+                idx = t.nin++;
+                t.in[idx] = rp;
+            }
+            t.coef[r][idx] += sgn;
+        };
+        const int rot[2] = {kj.e0, kj.e1};
+        for (int r = 0; r < 2 && rot[r] >= 0; ++r) {
+            const BrJob &b = L.br[rot[r]];
+            t.cst[r] = b.cst;
+            t.nrot = r + 1;
+            for (int w = 0; w < 2; ++w) {
+                const uint32_t *in = w ? b.in1 : b.in0;
+                const int32_t sgn = w ? b.s1 : b.s0;
+                auto it = in ? sums.find((uint64_t)(uintptr_t)in) : sums.end();
+                if (it != sums.end())
+                    for (int m = 0; m < it->second->n; ++m) term(r, it->second->in[m], it->second->s[m] * sgn);
+                else
+                    term(r, in, sgn);
+            }
         }
+        if (!ok) continue;
+        t.ks_cst = kj.cst;
+        t.out = resolve((uint64_t)(uintptr_t)kj.out, pool, phys);
+        t.rec = (int32_t)c->trace_next++;
+        F.tr.push_back(t);
+    }
+    if (F.tr.size() > to) F.launches.push_back({4, to, (int)(F.tr.size() - to)});
+}
+
+// Append one layer's jobs: its multi-input sums first, then chunks whose
+// blind rotations fit the extracted-row scratch (each followed by its key
+// switch and, when tracing, its trace copies); pointers are resolved against
+// `pool`.
+void flatten_layer(velopir_ctx *c, const Layer &L, int cap, uint32_t *pool, const std::vector<int> &phys, Flat &F)
+{
+    std::unordered_map<uint64_t, const SumJob *> sums;
+    if (!L.sm.empty()) {
+        const size_t so = F.sm.size();
+        for (const SumJob &x : L.sm) {
+            SumJob sj = x;
+            for (int k = 0; k < sj.n; ++k) sj.in[k] = resolve((uint64_t)(uintptr_t)sj.in[k], pool, phys);
+            sj.out = resolve((uint64_t)(uintptr_t)sj.out, pool, phys);
+            F.sm.push_back(sj);
+            if (c->trace_on) sums[(uint64_t)(uintptr_t)x.out] = &x;
+        }
+        F.launches.push_back({3, so, (int)L.sm.size()});
+    }
+    std::vector<Chunk> chunks;
+    layer_chunks(L, cap, chunks);
+    for (const Chunk &ch : chunks) {
         const size_t bo = F.br.size();
-        for (int b = br0; b < br1; ++b) {
+        for (int b = ch.br0; b < ch.br1; ++b) {
             BrJob j = L.br[b];
             j.in0 = j.in0 ? resolve((uint64_t)(uintptr_t)j.in0, pool, phys) : nullptr;
             j.in1 = j.in1 ? resolve((uint64_t)(uintptr_t)j.in1, pool, phys) : nullptr;
-            j.big = b - br0;
+            j.big = b - ch.br0;
             F.br.push_back(j);
         }
-        F.launches.push_back({0, bo, br1 - br0});
+        F.launches.push_back({0, bo, ch.br1 - ch.br0});
         const size_t ko = F.ks.size();
-        for (size_t q = g; q < g1; ++q) {
+        for (size_t q = ch.g0; q < ch.g1; ++q) {
             KsJob k = L.ks[q];
-            k.e0 -= br0;
-            if (k.e1 >= 0) k.e1 -= br0;
+            k.e0 -= ch.br0;
+            if (k.e1 >= 0) k.e1 -= ch.br0;
             k.out = resolve((uint64_t)(uintptr_t)k.out, pool, phys);
             F.ks.push_back(k);
         }
-        F.launches.push_back({1, ko, (int)(g1 - g)});
-        g = g1;
+        F.launches.push_back({1, ko, (int)(ch.g1 - ch.g0)});
+        if (c->trace_on) trace_chunk(c, L, ch, pool, phys, sums, F);
     }
 }
 
@@ -206,6 +319,13 @@ void flatten_free(const std::vector<FreeJob> &fr, uint32_t *pool, const std::vec
 int ensure_path_key(velopir_ctx *c)
 {
     if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    if (c->path == VP_PATH_TENSOR_F16 && !c->bk_tc_ready) {
+        int rc = ensure(c, c->bk_tc, bk_tc_bytes());
+        if (rc) return rc;
+        c->launches += prepare_bk_tc(as<uint32_t>(c->bk), c->bk_tc.p, c->stream);
+        CU(cudaGetLastError());
+        c->bk_tc_ready = true;
+    }
     if (c->path == VP_PATH_NTT && !c->bk_ntt_ready) {
         int rc = ensure(c, c->bk_ntt, bk_ntt_words() * 4);
         if (rc) return rc;
@@ -216,33 +336,49 @@ int ensure_path_key(velopir_ctx *c)
     return VELOPIR_OK;
 }
 
+// Scratch of the tensor-core path for launches of up to `rows` bootstraps;
+// sized before any launch is issued (and so before any stream capture).
+int ensure_tc_scratch(velopir_ctx *c, int rows)
+{
+    return c->path == VP_PATH_TENSOR_F16 ? ensure(c, c->tc_scratch, tc_scratch_bytes(std::max(2, rows))) : VELOPIR_OK;
+}
+
 int launch_br(velopir_ctx *c, const BrJob *jobs, int n)
 {
+    if (c->path == VP_PATH_TENSOR_F16)
+        return launch_br_tc(jobs, n, c->bk_tc.p, c->tc_scratch.p, as<uint32_t>(c->big), as<int>(c->errw), c->stream);
     if (c->path == VP_PATH_NTT)
         return launch_br_ntt(jobs, n, as<uint32_t>(c->bk_ntt), as<uint32_t>(c->big), as<int>(c->errw), c->stream);
     return launch_br_dense(jobs, n, as<uint32_t>(c->bk), as<uint32_t>(c->big), as<int>(c->errw), c->stream);
 }
 
-int upload(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+int upload(velopir_ctx *c, const Flat &F, const JobBufs &J)
 {
     int rc;
-    if ((rc = ensure(c, dbr, std::max<size_t>(1, F.br.size()) * sizeof(BrJob)))) return rc;
-    if ((rc = ensure(c, dks, std::max<size_t>(1, F.ks.size()) * sizeof(KsJob)))) return rc;
-    if ((rc = ensure(c, dfr, std::max<size_t>(1, F.fr.size()) * sizeof(FreeJob)))) return rc;
-    if (!F.br.empty()) CU(cudaMemcpyAsync(dbr.p, F.br.data(), F.br.size() * sizeof(BrJob), cudaMemcpyHostToDevice, c->stream));
-    if (!F.ks.empty()) CU(cudaMemcpyAsync(dks.p, F.ks.data(), F.ks.size() * sizeof(KsJob), cudaMemcpyHostToDevice, c->stream));
-    if (!F.fr.empty()) CU(cudaMemcpyAsync(dfr.p, F.fr.data(), F.fr.size() * sizeof(FreeJob), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = ensure(c, *J.br, std::max<size_t>(1, F.br.size()) * sizeof(BrJob)))) return rc;
+    if ((rc = ensure(c, *J.ks, std::max<size_t>(1, F.ks.size()) * sizeof(KsJob)))) return rc;
+    if ((rc = ensure(c, *J.fr, std::max<size_t>(1, F.fr.size()) * sizeof(FreeJob)))) return rc;
+    if ((rc = ensure(c, *J.sm, std::max<size_t>(1, F.sm.size()) * sizeof(SumJob)))) return rc;
+    if ((rc = ensure(c, *J.tr, std::max<size_t>(1, F.tr.size()) * sizeof(TraceJob)))) return rc;
+    if (!F.br.empty()) CU(cudaMemcpyAsync(J.br->p, F.br.data(), F.br.size() * sizeof(BrJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.ks.empty()) CU(cudaMemcpyAsync(J.ks->p, F.ks.data(), F.ks.size() * sizeof(KsJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.fr.empty()) CU(cudaMemcpyAsync(J.fr->p, F.fr.data(), F.fr.size() * sizeof(FreeJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.sm.empty()) CU(cudaMemcpyAsync(J.sm->p, F.sm.data(), F.sm.size() * sizeof(SumJob), cudaMemcpyHostToDevice, c->stream));
+    if (!F.tr.empty()) CU(cudaMemcpyAsync(J.tr->p, F.tr.data(), F.tr.size() * sizeof(TraceJob), cudaMemcpyHostToDevice, c->stream));
     return VELOPIR_OK;
 }
 
-int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr);
+int launches_only(velopir_ctx *c, const Flat &F, const JobBufs &J);
 
-// Upload the flattened jobs to (br, ks, fr) device buffers and issue every launch in order.
-int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+JobBufs program_bufs(velopir_ctx *c) { return {&c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->jobs_sm, &c->jobs_tr}; }
+JobBufs serving_bufs(velopir_ctx *c) { return {&c->s_br, &c->s_ks, &c->s_fr, &c->s_sm, &c->s_tr}; }
+
+// Upload the flattened jobs and issue every launch in order.
+int issue(velopir_ctx *c, const Flat &F, const JobBufs &J)
 {
     int rc;
-    if ((rc = upload(c, F, dbr, dks, dfr))) return rc;
-    return launches_only(c, F, dbr, dks, dfr);
+    if ((rc = upload(c, F, J))) return rc;
+    return launches_only(c, F, J);
 }
 
 // The launch sequence captured once into a CUDA graph and replayed; the job
@@ -251,15 +387,17 @@ int issue(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
 int issue_graph(velopir_ctx *c, const Flat &F)
 {
     int rc;
-    if ((rc = upload(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr))) return rc;
+    const JobBufs J = program_bufs(c);
+    if ((rc = upload(c, F, J))) return rc;
     std::vector<uint64_t> sig;
-    sig.reserve(F.launches.size() * 3 + 8);
+    sig.reserve(F.launches.size() * 3 + 12);
     for (const Launch &l : F.launches) {
         sig.push_back((uint64_t)l.kind);
         sig.push_back((uint64_t)l.off);
         sig.push_back((uint64_t)l.n);
     }
-    for (const DevBuf *b : {&c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->big, &c->bk, &c->bk_ntt, &c->ksk})
+    for (const DevBuf *b : {J.br, J.ks, J.fr, J.sm, J.tr, &c->big, &c->bk, &c->bk_ntt, &c->ksk, &c->trace_buf,
+                            &c->bk_tc, &c->tc_scratch})
         sig.push_back((uint64_t)(uintptr_t)b->p);
     sig.push_back((uint64_t)c->path);
     if (!c->graph_exec || sig != c->graph_sig) {
@@ -271,7 +409,7 @@ int issue_graph(velopir_ctx *c, const Flat &F)
         c->prof = false;
         cudaGraph_t g = nullptr;
         CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = launches_only(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr);
+        rc = launches_only(c, F, J);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         c->prof = prof;
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -287,10 +425,11 @@ int issue_graph(velopir_ctx *c, const Flat &F)
     return VELOPIR_OK;
 }
 
-int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBuf &dfr)
+int launches_only(velopir_ctx *c, const Flat &F, const JobBufs &J)
 {
     // one NVTX range per launch (kind and size) for timeline tools
-    static const char *names[3] = {"velopir:blind_rotate", "velopir:key_switch", "velopir:free_gates"};
+    static const char *names[5] = {"velopir:blind_rotate", "velopir:key_switch", "velopir:free_gates",
+                                   "velopir:sum_precombine", "velopir:gate_trace"};
     for (const Launch &l : F.launches) {
         nvtxRangePushA(names[l.kind]);
         cudaEvent_t ea = nullptr, eb = nullptr;
@@ -301,9 +440,16 @@ int launches_only(velopir_ctx *c, const Flat &F, DevBuf &dbr, DevBuf &dks, DevBu
             }
             CU(cudaEventRecord(ea, c->stream));
         }
-        if (l.kind == 0) c->launches += launch_br(c, as<BrJob>(dbr) + l.off, l.n);
-        else if (l.kind == 1) c->launches += launch_key_switch(as<KsJob>(dks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk), as<int>(c->errw), c->stream);
-        else c->launches += launch_free(as<FreeJob>(dfr) + l.off, l.n, c->stream);
+        switch (l.kind) {
+        case 0: c->launches += launch_br(c, as<BrJob>(*J.br) + l.off, l.n); break;
+        case 1:
+            c->launches += launch_key_switch(as<KsJob>(*J.ks) + l.off, l.n, as<uint32_t>(c->big), as<uint32_t>(c->ksk),
+                                             as<int>(c->errw), c->stream);
+            break;
+        case 2: c->launches += launch_free(as<FreeJob>(*J.fr) + l.off, l.n, c->stream); break;
+        case 3: c->launches += launch_sum(as<SumJob>(*J.sm) + l.off, l.n, c->stream); break;
+        default: c->launches += launch_trace(as<TraceJob>(*J.tr) + l.off, l.n, as<uint32_t>(c->trace_buf), c->stream); break;
+        }
         CU(cudaGetLastError());
         nvtxRangePop();
         if (c->prof) {
@@ -353,17 +499,18 @@ int run_program(velopir_ctx *c, Program &P, bool graph = false)
     if ((rc = ensure(c, c->pool, std::max<size_t>(1, (size_t)P.nphys) * kSlotWords * 4))) return rc;
     size_t max_br = 1;
     for (const Layer &L : P.layers) max_br = std::max(max_br, L.br.size());
-    const int cap = (int)std::max<size_t>(2, std::min<size_t>(max_br, (size_t)c->big_rows));
-    if ((rc = ensure(c, c->big, (size_t)cap * kBigWords * 4))) return rc;
+    const int cap = chunk_capacity(max_br, c->big_rows);
+    if ((rc = ensure(c, c->big, (size_t)std::max(2, cap) * kBigWords * 4))) return rc;
+    if ((rc = ensure_tc_scratch(c, cap))) return rc;
     uint32_t *pool = as<uint32_t>(c->pool);
     Flat F;
     flatten_free(P.pre, pool, P.phys, F);
     for (const Layer &L : P.layers) {
-        flatten_layer(L, cap, pool, P.phys, F);
+        flatten_layer(c, L, cap, pool, P.phys, F);
         flatten_free(L.fr, pool, P.phys, F);
     }
     if (graph) rc = issue_graph(c, F);
-    else rc = issue(c, F, c->jobs_br, c->jobs_ks, c->jobs_fr);
+    else rc = issue(c, F, program_bufs(c));
     if (rc) return rc;
     return check_device_error(c);
 }
@@ -441,6 +588,7 @@ struct ServeQuery {
     Program P;
     size_t cursor = 0;      // next layer
     size_t offset = 0;      // gates of layer `cursor` already issued
+    size_t sums_for = SIZE_MAX;   // layer whose multi-input sums were issued
     bool pre_done = false;
     size_t footprint = 0;
     uint32_t *dmem = nullptr;   // inputs + pool + output staging (one allocation)
@@ -451,6 +599,8 @@ struct ServeQuery {
     bool cancelled = false; // velopir_cancel: issue nothing more, report as cancelled
     cudaEvent_t ev = nullptr;
 };
+
+int agg_fanin(const velopir_query &q) { return q.agg_fanin >= 2 ? q.agg_fanin : 2; }
 
 size_t query_in_words(const velopir_query &q)
 {
@@ -476,6 +626,8 @@ int validate_query(velopir_ctx *c, const velopir_query &q)
         return fail(c, VELOPIR_ERR_ARG, "id_bits must be in [1, 32]");
     if (q.kind == VP_QUERY_IDM && q.payload && (q.payload_bits < 1 || q.payload_bits > 32))
         return fail(c, VELOPIR_ERR_ARG, "payload_bits must be in [1, 32]");
+    if (q.agg_fanin != 0 && (q.agg_fanin < 2 || q.agg_fanin > kMaxFanin))
+        return fail(c, VELOPIR_ERR_ARG, "agg_fanin must be 0 or in [2, %d]", kMaxFanin);
     return VELOPIR_OK;
 }
 
@@ -503,7 +655,7 @@ int build_query(velopir_ctx *c, ServeQuery &s)
         else if (q.kind == VP_QUERY_COV)
             build_cov(B, a.data(), q.db, q.D, out_base);
         else
-            build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out_base);
+            build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out_base, agg_fanin(q));
         if (c->path == VP_PATH_NTT) relayer(s.P, ntt_full_wave());
         allocate_slots(s.P);
         if (pass == 0) {
@@ -567,8 +719,9 @@ int serve_step(velopir_ctx *c)
     }
     const size_t wave = c->path == VP_PATH_NTT ? (size_t)ntt_full_wave() : 0;
     const size_t take = (wave && total_br >= wave) ? total_br / wave * wave : total_br;
-    const int cap = (int)std::max<size_t>(2, std::min<size_t>(take, (size_t)c->big_rows));
-    if ((rc = ensure(c, c->big, (size_t)cap * kBigWords * 4))) return rc;
+    const int cap = chunk_capacity(take, c->big_rows);
+    if ((rc = ensure(c, c->big, (size_t)std::max(2, cap) * kBigWords * 4))) return rc;
+    if ((rc = ensure_tc_scratch(c, cap))) return rc;
     // Merge layer jobs of all queries into one virtual layer with rebased indices.
     Layer ML;
     std::vector<FreeJob> pre, post;
@@ -585,6 +738,15 @@ int serve_step(velopir_ctx *c)
         }
         if (s.cancelled || s.cursor >= s.P.layers.size() || ML.br.size() >= take) continue;
         const Layer &L = s.P.layers[s.cursor];
+        // the layer's multi-input sums run before the first of its rotations
+        if (s.sums_for != s.cursor) {
+            for (SumJob sj : L.sm) {
+                for (int k = 0; k < sj.n; ++k) sj.in[k] = resolve((uint64_t)(uintptr_t)sj.in[k], pool, s.P.phys);
+                sj.out = resolve((uint64_t)(uintptr_t)sj.out, pool, s.P.phys);
+                ML.sm.push_back(sj);
+            }
+            s.sums_for = s.cursor;
+        }
         // a gate's blind rotations are consecutive, in the order of its key switches
         for (; s.offset < L.ks.size(); ++s.offset) {
             KsJob k = L.ks[s.offset];
@@ -614,9 +776,9 @@ int serve_step(velopir_ctx *c)
     }
     static const std::vector<int> nophys;
     flatten_free(pre, nullptr, nophys, merged);
-    flatten_layer(ML, cap, nullptr, nophys, merged);
+    flatten_layer(c, ML, cap, nullptr, nophys, merged);
     flatten_free(post, nullptr, nophys, merged);
-    if ((rc = issue(c, merged, c->s_br, c->s_ks, c->s_fr))) return rc;
+    if ((rc = issue(c, merged, serving_bufs(c)))) return rc;
     // completion bookkeeping
     for (auto &sp : c->active) {
         ServeQuery &s = *sp;
@@ -629,12 +791,15 @@ int serve_step(velopir_ctx *c)
     return VELOPIR_OK;
 }
 
-int reap(velopir_ctx *c)
+// Retire the admitted queries whose last work has finished.  sync_check
+// reads the device error word synchronously; the issue thread checks it per
+// step instead (without draining the stream).
+int reap(velopir_ctx *c, bool sync_check = true)
 {
     for (size_t i = 0; i < c->active.size();) {
         ServeQuery &s = *c->active[i];
         if (s.ev && cudaEventQuery(s.ev) == cudaSuccess) {
-            int rc = check_device_error(c);
+            int rc = sync_check ? check_device_error(c) : VELOPIR_OK;
             cudaEventDestroy(s.ev);
             s.ev = nullptr;
             cudaFreeAsync(s.dmem, c->stream);
@@ -650,6 +815,95 @@ int reap(velopir_ctx *c)
     return VELOPIR_OK;
 }
 
+// Whether any admitted query still has layers to issue.
+bool issuable(const velopir_ctx *c)
+{
+    for (const auto &sp : c->active)
+        if (!sp->cancelled && sp->cursor < sp->P.layers.size()) return true;
+    return false;
+}
+
+constexpr int kMaxInflightSteps = 2;
+
+// The issue thread: admits queries and issues serving steps back to back,
+// keeping up to kMaxInflightSteps steps queued on the stream so that the GPU
+// never waits for the host between steps.  After each step the error word is
+// copied into a pinned slot; a bounded wait that gave up is reported once the
+// step's event has completed.
+void issue_loop(velopir_ctx *c)
+{
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto retire_front = [&]() {
+        const velopir_ctx::Step st = c->inflight.front();
+        c->inflight.pop_front();
+        if (*st.err != kDevOk && c->issuer_rc == VELOPIR_OK) {
+            c->issuer_rc = VELOPIR_ERR_TIMEOUT;
+            c->issuer_err = "a bounded device wait gave up in a serving step";
+            cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->stream);
+        }
+        cudaEventDestroy(st.ev);
+    };
+    while (!c->stop_req) {
+        while (!c->inflight.empty() && cudaEventQuery(c->inflight.front().ev) == cudaSuccess) retire_front();
+        int rc = reap(c, false);
+        if (rc && c->issuer_rc == VELOPIR_OK) { c->issuer_rc = rc; c->issuer_err = c->err; }
+        if ((!c->waiting.empty() || issuable(c)) && (int)c->inflight.size() < kMaxInflightSteps &&
+            c->issuer_rc == VELOPIR_OK) {
+            rc = serve_step(c);
+            if (rc != VELOPIR_OK) {
+                c->issuer_rc = rc;
+                c->issuer_err = c->err;
+                continue;
+            }
+            // a slot of the pinned error copies that no in-flight step uses
+            int *slot = c->err_host;
+            for (int k = 0; k < kMaxInflightSteps; ++k) {
+                bool used = false;
+                for (const auto &st : c->inflight) used |= st.err == c->err_host + k;
+                if (!used) { slot = c->err_host + k; break; }
+            }
+            cudaEvent_t ev = nullptr;
+            if (cudaMemcpyAsync(slot, c->errw.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(ev, c->stream) != cudaSuccess) {
+                c->issuer_rc = VELOPIR_ERR_CUDA;
+                c->issuer_err = "serving step: event or copy failed";
+                if (ev) cudaEventDestroy(ev);
+                continue;
+            }
+            c->inflight.push_back({ev, slot});
+            continue;
+        }
+        if (!c->inflight.empty()) {
+            cudaEvent_t ev = c->inflight.front().ev;
+            lk.unlock();
+            cudaEventSynchronize(ev);
+            lk.lock();
+            continue;
+        }
+        bool pending = false;   // finished queries whose completion event is still outstanding
+        for (const auto &sp : c->active) pending |= sp->ev != nullptr;
+        lk.unlock();
+        if (pending) std::this_thread::sleep_for(std::chrono::microseconds(200));
+        else std::this_thread::sleep_for(std::chrono::milliseconds(1));
+        lk.lock();
+    }
+    while (!c->inflight.empty()) {
+        cudaEventSynchronize(c->inflight.front().ev);
+        retire_front();
+    }
+    reap(c, false);
+}
+
+// Entry points other than the serving calls refuse to run while the issue
+// thread owns the context's stream and scratch.
+int busy(velopir_ctx *c)
+{
+    return c->serving ? fail(c, VELOPIR_ERR_BUSY, "the serving issue thread owns this context (velopir_serve_stop)")
+                      : VELOPIR_OK;
+}
+
 }  // namespace
 
 // Internal accessors for entry points defined in other translation units.
@@ -658,6 +912,7 @@ namespace vp {
 int ctx_resources(velopir_ctx *c, CtxResources *r)
 {
     if (!c || !r) return VELOPIR_ERR_ARG;
+    if (int rc = busy(c)) return rc;
     r->device = c->device;
     r->stream = c->stream;
     r->key_loaded = c->key_loaded;
@@ -705,7 +960,7 @@ int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void 
         CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    if (configure_br_dense() != 0 || configure_br_ntt() != 0 || configure_key_switch() != 0)
+    if (configure_br_dense() != 0 || configure_br_ntt() != 0 || configure_br_tc() != 0 || configure_key_switch() != 0)
         return fail(nullptr, VELOPIR_ERR_CUDA, "cannot raise the shared-memory limit of the blind-rotation kernels");
     int rc = ensure(c, c->errw, 256);
     if (rc) { g_create_error = c->err; return rc; }
@@ -717,6 +972,7 @@ int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void 
 int velopir_destroy(velopir_ctx *c)
 {
     if (!c) return VELOPIR_OK;
+    velopir_serve_stop(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (auto &s : c->active) {
@@ -724,12 +980,14 @@ int velopir_destroy(velopir_ctx *c)
         if (s->dmem) cudaFreeAsync(s->dmem, c->stream);
     }
     cudaStreamSynchronize(c->stream);
-    DevBuf *bufs[] = {&c->bk, &c->ksk, &c->bk_ntt, &c->big, &c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->pool,
-                      &c->in, &c->out, &c->errw, &c->s_br, &c->s_ks, &c->s_fr};
+    DevBuf *bufs[] = {&c->bk, &c->ksk, &c->bk_ntt, &c->big, &c->jobs_br, &c->jobs_ks, &c->jobs_fr, &c->jobs_sm,
+                      &c->jobs_tr, &c->pool, &c->in, &c->out, &c->errw, &c->s_br, &c->s_ks, &c->s_fr, &c->s_sm,
+                      &c->s_tr, &c->trace_buf, &c->bk_tc, &c->tc_scratch};
     for (DevBuf *b : bufs) dev_free(c, *b);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->spare) cudaEventDestroy(e);
+    if (c->err_host) cudaFreeHost(c->err_host);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return VELOPIR_OK;
@@ -743,6 +1001,7 @@ int velopir_load_cloud_key(velopir_ctx *c, const velopir_params *params, const u
     if (!bk || !ksk) return fail(c, VELOPIR_ERR_ARG, "null key buffer");
     if (bk_words != kBkWords) return fail(c, VELOPIR_ERR_ARG, "bk_words %zu != %zu", bk_words, kBkWords);
     if (ksk_words != kKskAbiWords) return fail(c, VELOPIR_ERR_ARG, "ksk_words %zu != %zu", ksk_words, kKskAbiWords);
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     int rc;
     if ((rc = ensure(c, c->bk, kBkWords * 4))) return rc;
@@ -756,15 +1015,26 @@ int velopir_load_cloud_key(velopir_ctx *c, const velopir_params *params, const u
     CU(cudaStreamSynchronize(c->stream));
     c->key_loaded = true;
     c->bk_ntt_ready = false;
+    c->bk_tc_ready = false;
     return VELOPIR_OK;
 }
 
 int velopir_set_path(velopir_ctx *c, velopir_path path)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
-    if (path != VP_PATH_INT32_DENSE && !(path == VP_PATH_NTT && bk_ntt_words() > 0))
+    if (int rc = busy(c)) return rc;
+    if (path != VP_PATH_INT32_DENSE && path != VP_PATH_NTT && path != VP_PATH_TENSOR_F16)
         return fail(c, VELOPIR_ERR_ARG, "path %d is not available in this build", (int)path);
     c->path = path;
+    return VELOPIR_OK;
+}
+
+int velopir_set_launch_limit(velopir_ctx *c, size_t max_rotations)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
+    if (max_rotations > ((size_t)1 << 16)) return fail(c, VELOPIR_ERR_ARG, "max_rotations above 65536");
+    c->big_rows = max_rotations ? (int)max_rotations : (1 << 16);
     return VELOPIR_OK;
 }
 
@@ -772,6 +1042,7 @@ static int bootstrap_common(velopir_ctx *c, velopir_gate gate, const uint32_t *l
                             size_t count, bool plain)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     if ((int)gate < VP_AND || (int)gate > VP_MUX) return fail(c, VELOPIR_ERR_ARG, "unknown gate %d", (int)gate);
     if (count == 0) return VELOPIR_OK;
     if (!lwe_in || !lwe_out) return fail(c, VELOPIR_ERR_ARG, "null ciphertext buffer");
@@ -830,6 +1101,7 @@ static int host_plaintext(velopir_ctx *c, velopir_query &q, std::vector<uint32_t
 static int run_query(velopir_ctx *c, velopir_query q)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     int rc;
     if ((rc = validate_query(c, q))) return rc;
     std::vector<uint32_t> hdb, hpay;
@@ -858,7 +1130,7 @@ static int run_query(velopir_ctx *c, velopir_query q)
         for (int i = 0; i < 32; ++i) b[i] = B.input(din_b + (size_t)i * kLweWords);
     if (q.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), q.db, q.D, o.dev);
     else if (q.kind == VP_QUERY_COV) build_cov(B, a.data(), q.db, q.D, o.dev);
-    else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, o.dev);
+    else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, o.dev, agg_fanin(q));
     if ((rc = run_program(c, P))) return rc;
     return finish_out(c, o);
 }
@@ -866,6 +1138,7 @@ static int run_query(velopir_ctx *c, velopir_query q)
 int velopir_query_batch(velopir_ctx *c, const velopir_query *qs, size_t nq, int use_graph)
 {
     if (!c || (!qs && nq)) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    if (int rc = busy(c)) return rc;
     if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
     cudaSetDevice(c->device);
     int rc;
@@ -908,7 +1181,7 @@ int velopir_query_batch(velopir_ctx *c, const velopir_query *qs, size_t nq, int 
             for (int k = 0; k < 32; ++k) b[k] = B.input(db + (size_t)k * kLweWords);
         if (x.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), x.db, x.D, o.dev);
         else if (x.kind == VP_QUERY_COV) build_cov(B, a.data(), x.db, x.D, o.dev);
-        else build_idm(B, a.data(), x.id_bits, x.db, x.D, x.payload, x.payload_bits, o.dev);
+        else build_idm(B, a.data(), x.id_bits, x.db, x.D, x.payload, x.payload_bits, o.dev, agg_fanin(x));
     }
     if ((rc = run_program(c, P, use_graph != 0))) return rc;
     for (auto &o : outs)
@@ -921,6 +1194,7 @@ uint64_t velopir_graph_replays(velopir_ctx *c) { return c ? c->graph_replays : 0
 int velopir_autotune(velopir_ctx *c, double *wave_ms_out, int n_out)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     int rc;
     if ((rc = ensure_path_key(c))) return rc;
@@ -979,6 +1253,7 @@ int run_encdb(velopir_ctx *c, const uint32_t *q0, size_t q0_cts, const uint32_t 
               const uint32_t *db0, size_t db0_cts, const uint32_t *db1, size_t db1_cts, uint32_t *out,
               size_t out_cts, F build)
 {
+    if (int rc = busy(c)) return rc;
     if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
     cudaSetDevice(c->device);
     int rc;
@@ -1126,6 +1401,8 @@ int velopir_submit(velopir_ctx *c, const velopir_query *q, uint64_t *ticket)
             s->q.payload = s->payload.data();
         }
     }
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->waiting.size() >= 4096) return fail(c, VELOPIR_ERR_BUSY, "serving queue full");
     s->ticket = c->next_ticket++;
     *ticket = s->ticket;
     c->waiting.push_back(std::move(s));
@@ -1135,6 +1412,7 @@ int velopir_submit(velopir_ctx *c, const velopir_query *q, uint64_t *ticket)
 int velopir_cancel(velopir_ctx *c, uint64_t ticket)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     for (auto it = c->waiting.begin(); it != c->waiting.end(); ++it)
         if ((*it)->ticket == ticket) {   // never admitted: nothing on the device
@@ -1160,8 +1438,10 @@ int velopir_cancel(velopir_ctx *c, uint64_t ticket)
 int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
 {
     if (!c || !done) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     *done = 0;
+    if (c->serving && c->issuer_rc != VELOPIR_OK) return fail(c, c->issuer_rc, "%s", c->issuer_err.c_str());
     for (auto it = c->finished.begin(); it != c->finished.end(); ++it)
         if ((*it)->ticket == ticket) {
             *done = 1;
@@ -1174,6 +1454,7 @@ int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
     for (auto &s : c->active) known |= s->ticket == ticket;
     for (auto &s : c->waiting) known |= s->ticket == ticket;
     if (!known) return fail(c, VELOPIR_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    if (c->serving) return VELOPIR_OK;   // the issue thread steps the loop
     int rc = serve_step(c);
     if (rc) return rc;
     // keep at most one step in flight ahead of the host
@@ -1194,10 +1475,12 @@ int velopir_poll(velopir_ctx *c, uint64_t ticket, int *done)
 int velopir_progress(velopir_ctx *c, uint64_t *done, size_t cap, size_t *ndone)
 {
     if (!c || !ndone || (!done && cap)) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     *ndone = 0;
     int rc;
-    if (!c->waiting.empty() || !c->active.empty()) {
+    if (c->serving && c->issuer_rc != VELOPIR_OK) return fail(c, c->issuer_rc, "%s", c->issuer_err.c_str());
+    if (!c->serving && (!c->waiting.empty() || !c->active.empty())) {
         if ((rc = serve_step(c))) return rc;
         for (auto &s : c->active)
             if (s->ev) cudaEventSynchronize(s->ev);
@@ -1213,14 +1496,50 @@ int velopir_progress(velopir_ctx *c, uint64_t *done, size_t cap, size_t *ndone)
 int velopir_queue_depth(velopir_ctx *c, size_t *admitted, size_t *waiting)
 {
     if (!c || !admitted || !waiting) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(c->mu);
     *admitted = c->active.size();
     *waiting = c->waiting.size();
+    return VELOPIR_OK;
+}
+
+int velopir_serve_start(velopir_ctx *c)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (c->serving) return VELOPIR_OK;
+    if (!c->key_loaded) return fail(c, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    cudaSetDevice(c->device);
+    int rc;
+    if ((rc = ensure_path_key(c))) return rc;
+    if (!c->err_host) CU(cudaMallocHost(&c->err_host, kMaxInflightSteps * sizeof(int)));
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stop_req = false;
+    c->issuer_rc = VELOPIR_OK;
+    c->issuer_err.clear();
+    c->serving = true;
+    c->issuer = std::thread(issue_loop, c);
+    return VELOPIR_OK;
+}
+
+int velopir_serve_stop(velopir_ctx *c)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (!c->serving) return VELOPIR_OK;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stop_req = true;
+    }
+    c->issuer.join();
+    c->serving = false;
+    const int rc = c->issuer_rc;
+    c->issuer_rc = VELOPIR_OK;
+    if (rc != VELOPIR_OK) return fail(c, rc, "%s", c->issuer_err.c_str());
     return VELOPIR_OK;
 }
 
 int velopir_sync(velopir_ctx *c)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     CU(cudaStreamSynchronize(c->stream));
     return check_device_error(c);
@@ -1233,26 +1552,65 @@ uint64_t velopir_launch_count(velopir_ctx *c) { return c ? c->launches : 0; }
 int velopir_selftest_wait_timeout(velopir_ctx *c)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     c->launches += launch_wait_selftest(as<int>(c->errw), c->stream);
     CU(cudaGetLastError());
     return check_device_error(c);
 }
 
+int velopir_trace_start(velopir_ctx *c, uint64_t seed, uint32_t per_launch, uint32_t one_in, size_t cap)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
+    if ((per_launch == 0 && one_in == 0) || cap == 0 || cap > ((size_t)1 << 20))
+        return fail(c, VELOPIR_ERR_ARG, "per_launch or one_in must be >= 1, and cap in [1, 2^20]");
+    cudaSetDevice(c->device);
+    const size_t bytes = cap * (size_t)kTraceWords * 4;
+    int rc;
+    if ((rc = ensure(c, c->trace_buf, bytes))) return rc;
+    CU(cudaMemsetAsync(c->trace_buf.p, 0, bytes, c->stream));
+    c->trace_on = true;
+    c->trace_rng = seed;
+    c->trace_per_launch = per_launch;
+    c->trace_one_in = one_in;
+    c->trace_cap = cap;
+    c->trace_next = 0;
+    return VELOPIR_OK;
+}
+
+int velopir_trace_stop(velopir_ctx *c, velopir_trace_rec *out, size_t cap, size_t *count)
+{
+    if (!c || !count || (!out && cap)) return fail(c, VELOPIR_ERR_ARG, "null argument");
+    if (int rc = busy(c)) return rc;
+    cudaSetDevice(c->device);
+    *count = c->trace_on ? c->trace_next : 0;
+    if (c->trace_on) {
+        const size_t n = std::min(cap, c->trace_next);
+        if (n) CU(cudaMemcpyAsync(out, c->trace_buf.p, n * sizeof(velopir_trace_rec), cudaMemcpyDefault, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    c->trace_on = false;
+    dev_free(c, c->trace_buf);
+    return check_device_error(c);
+}
+
 int velopir_profile(velopir_ctx *c, int enable)
 {
     if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     int rc = prof_drain(c);
     if (rc) return rc;
-    for (int k = 0; k < 3; ++k) { c->prof_launches[k] = c->prof_units[k] = 0; c->prof_ms[k] = 0; }
+    for (int k = 0; k < 5; ++k) { c->prof_launches[k] = c->prof_units[k] = 0; c->prof_ms[k] = 0; }
     c->prof = enable != 0;
     return VELOPIR_OK;
 }
 
 int velopir_profile_read(velopir_ctx *c, int kernel, uint64_t *launches, uint64_t *units, double *ms)
 {
-    if (!c || kernel < 0 || kernel > 2 || !launches || !units || !ms) return fail(c, VELOPIR_ERR_ARG, "bad argument");
+    if (!c || kernel < 0 || kernel > 4 || !launches || !units || !ms) return fail(c, VELOPIR_ERR_ARG, "bad argument");
+    if (int rc = busy(c)) return rc;
     cudaSetDevice(c->device);
     int rc = prof_drain(c);
     if (rc) return rc;

@@ -1,6 +1,8 @@
-// Client side of VeLoPIR (host only): key generation, encryption and
-// decryption from caller-supplied random numbers (paper Section 2.2: KeyGen,
-// Enc with Ecd: m -> m/4 - 1/8, Dec by the sign of the phase).
+// libvelopir_client.so, the host-only side of VeLoPIR (velopir_client.h): key
+// generation, encryption and decryption from caller-supplied random numbers
+// (paper Section 2.2: KeyGen, Enc with Ecd: m -> m/4 - 1/8, Dec by the sign of
+// the phase), Alg. PubKeyGen and Alg. ServerEnc.  Plain C++: built with the
+// host compiler, linked against no CUDA library.
 //
 // The TRLWE mask products a(X) * K(X) use the binary key directly: the
 // product is the signed sum of the negacyclic shifts X^i a(X) over the set
@@ -10,7 +12,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/velopir.h"
+#include "../../include/velopir_client.h"
 
 namespace {
 

@@ -199,6 +199,43 @@ __global__ void free_gate_kernel(const FreeJob *__restrict__ jobs, int njobs)
     }
 }
 
+// out = sum_k s[k] in[k]: the multi-input pre-combinations of a layer.
+__global__ void sum_kernel(const SumJob *__restrict__ jobs, int njobs)
+{
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    const SumJob sj = jobs[j];
+    for (int w = threadIdx.x; w < kLweWords; w += blockDim.x) {
+        uint32_t v = 0u;
+        for (int k = 0; k < sj.n; ++k) v += (uint32_t)sj.s[k] * sj.in[k][w];
+        sj.out[w] = v;
+    }
+}
+
+// Gate trace: one record of kTraceWords words per sampled gate (the layout of
+// velopir_trace_rec): header, then the inputs (zero beyond nin), then the output.
+
+__global__ void trace_kernel(const TraceJob *__restrict__ jobs, int njobs, uint32_t *__restrict__ records)
+{
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    const TraceJob &t = jobs[j];
+    uint32_t *r = records + (size_t)t.rec * kTraceWords;
+    if (threadIdx.x == 0) {
+        r[0] = (uint32_t)t.nrot;
+        r[1] = (uint32_t)t.nin;
+        r[2] = t.ks_cst;
+        r[3] = t.cst[0];
+        r[4] = t.cst[1];
+    }
+    if (threadIdx.x < 2 * kSumMax) r[5 + threadIdx.x] = (uint32_t)t.coef[threadIdx.x / kSumMax][threadIdx.x % kSumMax];
+    for (int k = 0; k <= kSumMax; ++k) {
+        const uint32_t *src = k < kSumMax ? (k < t.nin ? t.in[k] : nullptr) : t.out;
+        uint32_t *dst = r + kTraceHead + (size_t)k * kLweWords;
+        for (int w = threadIdx.x; w < kLweWords; w += blockDim.x) dst[w] = src ? src[w] : 0u;
+    }
+}
+
 __global__ void pad_ksk_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, size_t rows)
 {
     const size_t r = blockIdx.x;
@@ -244,6 +281,20 @@ int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st)
 {
     if (njobs <= 0) return 0;
     free_gate_kernel<<<njobs, 128, 0, st>>>(jobs, njobs);
+    return 1;
+}
+
+int launch_sum(const SumJob *jobs, int njobs, cudaStream_t st)
+{
+    if (njobs <= 0) return 0;
+    sum_kernel<<<njobs, 128, 0, st>>>(jobs, njobs);
+    return 1;
+}
+
+int launch_trace(const TraceJob *jobs, int njobs, uint32_t *records, cudaStream_t st)
+{
+    if (njobs <= 0) return 0;
+    trace_kernel<<<njobs, 128, 0, st>>>(jobs, njobs, records);
     return 1;
 }
 

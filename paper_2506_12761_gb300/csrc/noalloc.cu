@@ -91,12 +91,12 @@ extern "C" int velopir_bootstrap_batch_noalloc(velopir_ctx *ctx, velopir_gate ga
                         "count exceeds VELOPIR_NOALLOC_MAX_GATES (256): split the batch or use velopir_bootstrap_batch");
     if (!lwe_in || !lwe_out) return ctx_fail(ctx, VELOPIR_ERR_ARG, "null ciphertext buffer");
     CtxResources R{};
-    ctx_resources(ctx, &R);
+    if (int rc = ctx_resources(ctx, &R)) return rc;
     if (!R.key_loaded) return ctx_fail(ctx, VELOPIR_ERR_NOKEY, "no cloud key loaded");
+    if (R.device < 0 || R.device >= 256) return ctx_fail(ctx, VELOPIR_ERR_ARG, "device index out of range");
     if (cudaSetDevice(R.device) != cudaSuccess) return ctx_fail(ctx, VELOPIR_ERR_CUDA, "cudaSetDevice failed");
     if (!on_device(lwe_in) || !on_device(lwe_out))
         return ctx_fail(ctx, VELOPIR_ERR_ARG, "lwe_in and lwe_out must be device memory for the no-allocation call");
-    if (R.device < 0 || R.device >= 256) return ctx_fail(ctx, VELOPIR_ERR_ARG, "device index out of range");
 
     NoAllocScratch *S;
     {

@@ -68,39 +68,39 @@ struct Exec {
     }
 };
 
-// Execute a scheduled program in the device's launch order: each launch is
-// split into chunks of at most chunk_rows blind rotations (0: one chunk), as
-// the executor splits launches to fit its extracted-row scratch, and every
-// chunk's blind rotations read before its key switches write.
+// Execute a scheduled program in the device's launch order: a layer's
+// multi-input sums first, then its gates in the executor's chunks (the shared
+// layer_chunks for a scratch of chunk_rows rows, clamped as the executor
+// clamps it; 0: one chunk per layer), every chunk's blind rotations reading
+// before its key switches write.  launch_sizes[l] receives the blind
+// rotations of layer l.
 void execute(const Program &P, Exec &X, int chunk_rows, size_t *launch_sizes, int max_launches)
 {
     X.free_jobs(P.pre);
+    size_t max_br = 1;
+    for (const Layer &L : P.layers) max_br = std::max(max_br, L.br.size());
+    const int cap = chunk_rows > 0 ? chunk_capacity(max_br, chunk_rows) : 0;
     std::vector<uint32_t> ext;
+    std::vector<Chunk> chunks;
     for (size_t l = 0; l < P.layers.size(); ++l) {
         const Layer &L = P.layers[l];
-        const size_t nks = L.ks.size();
-        size_t g = 0;
-        while (g < nks) {
-            const int br0 = L.ks[g].e0;
-            size_t g1 = g;
-            int br1 = br0;
-            while (g1 < nks) {
-                const int hi = std::max(L.ks[g1].e0, L.ks[g1].e1) + 1;
-                if (chunk_rows > 0 && hi - br0 > chunk_rows && g1 > g) break;
-                br1 = std::max(br1, hi);
-                ++g1;
-            }
-            ext.assign((size_t)(br1 - br0), 0u);
-            for (int r = br0; r < br1; ++r) {
+        for (const SumJob &sj : L.sm) {
+            uint32_t v = 0u;
+            for (int k = 0; k < sj.n; ++k) v += (uint32_t)sj.s[k] * X.read(sj.in[k]);
+            X.write(sj.out, v);
+        }
+        layer_chunks(L, cap, chunks);
+        for (const Chunk &ch : chunks) {
+            ext.assign((size_t)(ch.br1 - ch.br0), 0u);
+            for (int r = ch.br0; r < ch.br1; ++r) {
                 const BrJob &j = L.br[r];
                 const uint32_t c = j.cst + (uint32_t)j.s0 * X.read(j.in0) + (uint32_t)j.s1 * X.read(j.in1);
-                ext[r - br0] = (int32_t)c >= 0 ? kMu : 0u - kMu;
+                ext[r - ch.br0] = (int32_t)c >= 0 ? kMu : 0u - kMu;
             }
-            for (size_t q = g; q < g1; ++q) {
+            for (size_t q = ch.g0; q < ch.g1; ++q) {
                 const KsJob &k = L.ks[q];
-                X.write(k.out, ext[k.e0 - br0] + (k.e1 >= 0 ? ext[k.e1 - br0] : 0u) + k.cst);
+                X.write(k.out, ext[k.e0 - ch.br0] + (k.e1 >= 0 ? ext[k.e1 - ch.br0] : 0u) + k.cst);
             }
-            g = g1;
         }
         X.free_jobs(L.fr);
         if (launch_sizes && (int)l < max_launches) launch_sizes[l] = L.br.size();
@@ -113,6 +113,7 @@ bool plain_kind_ok(const velopir_query &q)
     if (q.kind != VP_QUERY_INTV && q.kind != VP_QUERY_COV && q.kind != VP_QUERY_IDM) return false;
     if (q.kind == VP_QUERY_IDM && (q.id_bits < 1 || q.id_bits > 32)) return false;
     if (q.payload && (q.kind != VP_QUERY_IDM || q.payload_bits < 1 || q.payload_bits > 32)) return false;
+    if (q.agg_fanin != 0 && (q.agg_fanin < 2 || q.agg_fanin > kMaxFanin)) return false;
     return true;
 }
 
@@ -151,7 +152,8 @@ extern "C" int velopir_plan_batch(const velopir_query *qs, size_t nq, int wave, 
         }
         if (q.kind == VP_QUERY_INTV) build_intv(B, a.data(), b.data(), q.db, q.D, out);
         else if (q.kind == VP_QUERY_COV) build_cov(B, a.data(), q.db, q.D, out);
-        else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out);
+        else build_idm(B, a.data(), q.id_bits, q.db, q.D, q.payload, q.payload_bits, out,
+                       q.agg_fanin >= 2 ? q.agg_fanin : 2);
         const size_t nout = plan_out_bits(q);
         for (size_t k = 0; k < nout; ++k) outs.push_back(out + k * kLweWords);
         ino += (na + nb) * kLweWords;
@@ -181,6 +183,8 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
     if (kind == VP_PLAN_COV_ENCDB && (width < 1 || width > 16)) return VELOPIR_ERR_ARG;
     if (q->payload && (q->payload_bits < 1 || q->payload_bits > 32)) return VELOPIR_ERR_ARG;
     if (q->payload && (kind == VP_QUERY_INTV || kind == VP_QUERY_COV)) return VELOPIR_ERR_ARG;   // no payload form
+    if (q->agg_fanin != 0 && (q->agg_fanin < 2 || q->agg_fanin > kMaxFanin || kind != VP_QUERY_IDM))
+        return VELOPIR_ERR_ARG;
     if (launch_sizes && max_launches < 0) return VELOPIR_ERR_ARG;
 
     // stand-in device addresses: distinct, 16-byte aligned, never dereferenced
@@ -203,7 +207,10 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
     switch (kind) {
     case VP_QUERY_INTV: build_intv(B, a.data(), b.data(), q->db, q->D, out); break;
     case VP_QUERY_COV: build_cov(B, a.data(), q->db, q->D, out); break;
-    case VP_QUERY_IDM: build_idm(B, a.data(), width, q->db, q->D, q->payload, q->payload_bits, out); break;
+    case VP_QUERY_IDM:
+        build_idm(B, a.data(), width, q->db, q->D, q->payload, q->payload_bits, out,
+                  q->agg_fanin >= 2 ? q->agg_fanin : 2);
+        break;
     case VP_PLAN_INTV_ENCDB:
         build_intv_enc(B, a.data(), b.data(), width, edb, q->D, pb ? epay : nullptr, pb, out);
         break;

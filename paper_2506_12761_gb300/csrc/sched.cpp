@@ -116,6 +116,55 @@ Ref Builder::mux(const Ref &c, const Ref &a, const Ref &b, uint32_t *out)
     return r;
 }
 
+Ref Builder::xor_many(const Ref *in, int g, uint32_t *out)
+{
+    // One bootstrap of 2 sum_k c_k + T((g-1)/4): phase +1/4 when an odd number
+    // of inputs is true, -1/4 when even (g = 2 is the XOR gate's combination).
+    int l = 0;
+    for (int k = 0; k < g; ++k) l = std::max(l, in[k].ready);
+    BrJob j{};
+    j.cst = (uint32_t)(g - 1) * (2 * kMu);
+    const uint32_t *src[kSumMax];
+    int32_t sg[kSumMax];
+    int nt = 0;
+    for (int k = 0; k < g; ++k) {
+        j.cst += 2u * in[k].cst;
+        if (in[k].src) {
+            src[nt] = reinterpret_cast<const uint32_t *>(in[k].src);
+            sg[nt++] = 2 * in[k].sign;
+        }
+        use(in[k], l);
+    }
+    if (nt <= 2) {
+        if (nt > 0) { j.in0 = src[0]; j.s0 = sg[0]; }
+        if (nt > 1) { j.in1 = src[1]; j.s1 = sg[1]; }
+    } else {
+        const uint64_t t = kSlotTag | (uint64_t)new_slot(l);   // read by this gate's rotation only
+        SumJob sj{};
+        for (int k = 0; k < nt; ++k) { sj.in[k] = src[k]; sj.s[k] = sg[k]; }
+        sj.n = nt;
+        sj.out = reinterpret_cast<uint32_t *>(t);
+        layer(l).sm.push_back(sj);
+        j.in0 = reinterpret_cast<const uint32_t *>(t);
+        j.s0 = 1;
+    }
+    Layer &L = layer(l);
+    KsJob k{};
+    k.e0 = (int32_t)L.br.size();
+    k.e1 = -1;
+    L.br.push_back(j);
+    const uint64_t dst = out ? (uint64_t)(uintptr_t)out : (kSlotTag | (uint64_t)new_slot(l));
+    k.out = reinterpret_cast<uint32_t *>(dst);
+    L.ks.push_back(k);
+    P.bootstraps += 1;
+    P.gates += 1;
+    Ref r;
+    r.src = dst;
+    r.sign = 1;
+    r.ready = l + 1;
+    return r;
+}
+
 void Builder::materialize(const Ref &r, uint32_t *out)
 {
     FreeJob f{};
@@ -194,7 +243,7 @@ void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uin
 }
 
 void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
-               int payload_bits, uint32_t *out)
+               int payload_bits, uint32_t *out, int fanin)
 {
     if (!payload) {
         for (size_t d = 0; d < D; ++d) build_eq_plain(B, id, id_bits, ids[d], out + d * kLweWords);
@@ -209,14 +258,33 @@ void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size
     for (size_t d = 0; d < D; ++d)
         for (int j = 0; j < payload_bits; ++j)
             S[d * payload_bits + j] = ((payload[d] >> j) & 1u) ? v[d] : Builder::trivial(0u - kMu);
-    size_t last_k = 0;
-    for (size_t k = 1; k < D; k *= 2) last_k = k;
-    for (size_t k = 1; k < D; k *= 2)
-        for (size_t i = 0; i + k < D; i += 2 * k)
-            for (int j = 0; j < payload_bits; ++j) {
-                uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
-                S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
+    if (fanin > 2) {
+        // Fan-in-g tree: for k = 1, g, g^2, ... the members i, i + k, ...,
+        // i + (g-1)k (those below D) of each group are XORed with one
+        // bootstrap into member i; the level with g k >= D writes `out`.
+        const size_t g = (size_t)std::min(fanin, kMaxFanin);
+        Ref grp[kMaxFanin];
+        for (size_t k = 1; k < D; k *= g)
+            for (size_t i = 0; i < D; i += g * k) {
+                size_t m = 0;
+                while (m < g && i + m * k < D) ++m;
+                if (m < 2) continue;
+                for (int j = 0; j < payload_bits; ++j) {
+                    for (size_t q = 0; q < m; ++q) grp[q] = S[(i + q * k) * payload_bits + j];
+                    uint32_t *o = (g * k >= D && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                    S[i * payload_bits + j] = B.xor_many(grp, (int)m, o);
+                }
             }
+    } else {
+        size_t last_k = 0;
+        for (size_t k = 1; k < D; k *= 2) last_k = k;
+        for (size_t k = 1; k < D; k *= 2)
+            for (size_t i = 0; i + k < D; i += 2 * k)
+                for (int j = 0; j < payload_bits; ++j) {
+                    uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                    S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
+                }
+    }
     if (D == 1)
         for (int j = 0; j < payload_bits; ++j) B.materialize(S[j], out + (size_t)j * kLweWords);
 }
@@ -328,6 +396,33 @@ void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_i
     if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
 }
 
+void layer_chunks(const Layer &L, int cap, std::vector<Chunk> &out)
+{
+    out.clear();
+    const size_t nks = L.ks.size();
+    size_t g = 0;
+    while (g < nks) {
+        const int br0 = L.ks[g].e0;
+        size_t g1 = g;
+        int br1 = br0;
+        while (g1 < nks) {
+            const int hi = std::max(L.ks[g1].e0, L.ks[g1].e1) + 1;
+            if (cap > 0 && hi - br0 > cap && g1 > g) break;
+            br1 = std::max(br1, hi);
+            ++g1;
+        }
+        out.push_back({g, g1, br0, br1});
+        g = g1;
+    }
+}
+
+int chunk_capacity(size_t max_br, int limit)
+{
+    // a chunk always holds a whole gate, so a MUX's two rotations need two
+    // rows of scratch even under a limit of one
+    return (int)std::min<size_t>(std::max<size_t>(1, max_br), (size_t)std::max(1, limit));
+}
+
 void relayer(Program &p, int wave)
 {
     if (wave <= 0 || p.layers.size() <= 1) return;
@@ -368,32 +463,51 @@ void relayer(Program &p, int wave)
         }
     }
     const int ng = (int)g.size();
-    // predecessors (at most 4: two rotations x two inputs), then successors in CSR form
-    std::vector<int> pred(4 * (size_t)ng, -1);
+    // The multi-input pre-combination feeding a rotation, by its pool slot.
+    std::unordered_map<uint64_t, const SumJob *> sum_of;
+    for (const Layer &L : p.layers)
+        for (const SumJob &sj : L.sm) sum_of[(uint64_t)(uintptr_t)sj.out] = &sj;
+    auto sum_for = [&](const uint32_t *in) -> const SumJob * {
+        if (sum_of.empty() || !in) return nullptr;
+        auto it = sum_of.find((uint64_t)(uintptr_t)in);
+        return it == sum_of.end() ? nullptr : it->second;
+    };
+    // predecessors (at most 2 rotations x 2 inputs, or the kSumMax inputs of
+    // a pre-combination), then successors in CSR form
+    constexpr int kMaxPred = 2 * kSumMax;
+    std::vector<int> pred(kMaxPred * (size_t)ng, -1);
     std::vector<int> nsucc(ng + 1, 0);
     for (int i = 0; i < ng; ++i) {
         const Layer &L = p.layers[g[i].layer];
         const KsJob &k = L.ks[g[i].ks];
         int np = 0;
+        auto add = [&](const uint32_t *in) {
+            const int q = prod_of(in);
+            if (q < 0 || q == i) return;
+            bool dup = false;
+            for (int t = 0; t < np; ++t) dup |= pred[kMaxPred * (size_t)i + t] == q;
+            if (!dup && np < kMaxPred) pred[kMaxPred * (size_t)i + np++] = q;
+        };
         for (int e : {k.e0, k.e1}) {
             if (e < 0) continue;
             for (const uint32_t *in : {L.br[e].in0, L.br[e].in1}) {
-                const int q = prod_of(in);
-                if (q < 0 || q == i) continue;
-                bool dup = false;
-                for (int t = 0; t < np; ++t) dup |= pred[4 * (size_t)i + t] == q;
-                if (!dup) pred[4 * (size_t)i + np++] = q;
+                if (const SumJob *sj = sum_for(in)) {
+                    for (int t = 0; t < sj->n; ++t) add(sj->in[t]);
+                } else {
+                    add(in);
+                }
             }
         }
         g[i].indeg = np;
-        for (int t = 0; t < np; ++t) nsucc[pred[4 * (size_t)i + t] + 1]++;
+        for (int t = 0; t < np; ++t) nsucc[pred[kMaxPred * (size_t)i + t] + 1]++;
     }
     for (int i = 0; i < ng; ++i) nsucc[i + 1] += nsucc[i];
     std::vector<int> succ(nsucc[ng]);
     {
         std::vector<int> fill(nsucc.begin(), nsucc.end() - 1);
         for (int i = 0; i < ng; ++i)
-            for (int t = 0; t < 4 && pred[4 * (size_t)i + t] >= 0; ++t) succ[fill[pred[4 * (size_t)i + t]]++] = i;
+            for (int t = 0; t < kMaxPred && pred[kMaxPred * (size_t)i + t] >= 0; ++t)
+                succ[fill[pred[kMaxPred * (size_t)i + t]]++] = i;
     }
     // longest chain of gates from each gate to the end (producers precede
     // consumers in the ASAP order, so a reverse sweep sees successors first)
@@ -461,6 +575,10 @@ void relayer(Program &p, int wave)
             const int e0 = (int)NL[t].br.size();
             NL[t].br.push_back(L.br[k.e0]);
             if (k.e1 >= 0) NL[t].br.push_back(L.br[k.e1]);
+            for (int e : {k.e0, k.e1})   // a rotation's pre-combination runs in its launch
+                if (e >= 0)
+                    for (const uint32_t *in : {L.br[e].in0, L.br[e].in1})
+                        if (const SumJob *sj = sum_for(in)) NL[t].sm.push_back(*sj);
             k.e0 = e0;
             k.e1 = k.e1 >= 0 ? e0 + 1 : -1;
             NL[t].ks.push_back(k);
@@ -474,9 +592,14 @@ void relayer(Program &p, int wave)
         const Layer &L = p.layers[l];
         for (const KsJob &k : L.ks)
             if (int v = slot_of(k.out); v >= 0) p.slot_def[v] = p.slot_last[v] = l;
+        for (const SumJob &sj : L.sm)
+            if (int v = slot_of(sj.out); v >= 0) p.slot_def[v] = p.slot_last[v] = l;
     }
     for (int l = 0; l < (int)p.layers.size(); ++l) {
         const Layer &L = p.layers[l];
+        for (const SumJob &sj : L.sm)
+            for (int t = 0; t < sj.n; ++t)
+                if (int v = slot_of(sj.in[t]); v >= 0) p.slot_last[v] = std::max(p.slot_last[v], l);
         for (const BrJob &j : L.br)
             for (const uint32_t *in : {j.in0, j.in1})
                 if (int v = in ? slot_of(in) : -1; v >= 0) p.slot_last[v] = std::max(p.slot_last[v], l);

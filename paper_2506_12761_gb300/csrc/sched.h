@@ -27,10 +27,26 @@ struct Ref {
 };
 
 struct Layer {
+    std::vector<SumJob> sm;  // multi-input pre-combinations, run before this layer's blind rotations
     std::vector<BrJob> br;   // pointers may carry kSlotTag
     std::vector<KsJob> ks;   // e0/e1 index `br` of this layer
     std::vector<FreeJob> fr; // run after this layer's key switches
 };
+
+// The executor splits a layer into chunks whose blind rotations fit its
+// extracted-row scratch: gates [g0, g1) of L.ks with rotations [br0, br1).
+struct Chunk {
+    size_t g0, g1;
+    int br0, br1;
+};
+// Chunks of L for a scratch of `cap` rows (cap <= 0: one chunk).  A gate's
+// rotations are never split; a chunk holds at least one gate.
+void layer_chunks(const Layer &L, int cap, std::vector<Chunk> &out);
+// Chunk size (rotations) of the executor for a program whose largest layer
+// has max_br rotations, given a limit of `limit` per launch.  A chunk exceeds
+// it only to keep a MUX's two rotations together, so the scratch holds
+// max(2, chunk_capacity) rows.
+int chunk_capacity(size_t max_br, int limit);
 
 struct Program {
     std::vector<Layer> layers;
@@ -58,6 +74,10 @@ public:
     Ref gate(int g, const Ref &a, const Ref &b, uint32_t *out = nullptr);
     // MUX(c, a, b) = c ? a : b with two blind rotations and one key switch.
     Ref mux(const Ref &c, const Ref &a, const Ref &b, uint32_t *out = nullptr);
+    // XOR of g >= 2 values with one bootstrap of 2 sum_k in_k + T((g-1)/4)
+    // (the fan-in-g HomSum node); more than two stored inputs are summed by a
+    // SumJob into a pool slot first.
+    Ref xor_many(const Ref *in, int g, uint32_t *out = nullptr);
     // Write the value of a Ref into `out` (device) without a bootstrap.
     void materialize(const Ref &r, uint32_t *out);
 
@@ -74,8 +94,12 @@ Ref build_compare(Builder &B, const Ref *x, int l, uint64_t plain, bool plain_fi
 Ref build_eq_plain(Builder &B, const Ref *x, int l, uint64_t v, uint32_t *out = nullptr);
 void build_intv(Builder &B, const Ref *x, const Ref *y, const uint32_t *rects, size_t D, uint32_t *out);
 void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uint32_t *out);
+// With a payload, the zeroed payloads are XOR-aggregated by a tree of
+// fan-in `fanin` (2: the pairwise HomSum of Section 5; 3..8: one bootstrap
+// per fanin inputs).
 void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
-               int payload_bits, uint32_t *out);
+               int payload_bits, uint32_t *out, int fanin = 2);
+constexpr int kMaxFanin = kSumMax;
 
 // Circuits with an encrypted database (the paper's protocol: Alg. ServerEnc
 // encrypts every database bit).  Database operands are ciphertexts (device

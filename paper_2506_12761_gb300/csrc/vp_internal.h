@@ -63,6 +63,38 @@ struct FreeJob {
 };
 static_assert(sizeof(FreeJob) == 32, "FreeJob layout");
 
+// A multi-input linear pre-combination materialised before a layer's blind
+// rotations (the g-input XOR of the fan-in HomSum): out = sum_k s[k] in[k]
+// over the first n terms.  The blind rotation that reads `out` adds the
+// gate's constant.
+constexpr int kSumMax = 8;
+struct SumJob {
+    const uint32_t *in[kSumMax];
+    int32_t s[kSumMax];
+    uint32_t *out;
+    int32_t n;
+    uint32_t pad;
+};
+static_assert(sizeof(SumJob) == 112, "SumJob layout");
+
+// One sampled gate of the gate trace: copy its inputs and output into record
+// `rec` of the trace buffer, with its pre-combination (the layout of
+// velopir_trace_rec).
+struct TraceJob {
+    const uint32_t *in[kSumMax];
+    const uint32_t *out;
+    int32_t coef[2][kSumMax];
+    uint32_t cst[2];
+    uint32_t ks_cst;
+    int32_t nrot, nin;
+    int32_t rec;
+};
+static_assert(sizeof(TraceJob) == 160, "TraceJob layout");
+// Words of one trace record: nrot, nin, ks_cst, cst[2], coef[2][kSumMax],
+// in[kSumMax][kLweWords], out[kLweWords].
+constexpr int kTraceHead = 5 + 2 * kSumMax;
+constexpr int kTraceWords = kTraceHead + (kSumMax + 1) * kLweWords;
+
 // Device-side error codes written to the context's error word.
 enum : int { kDevOk = 0, kDevTimeout = 1 };
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of every device-side wait (2 s)
@@ -86,10 +118,20 @@ void ntt_set_wave_ms(int warps, float ms);     // record a measured full-wave ti
 int ntt_full_wave();                           // bootstraps in one full wave of the best tuned shape (0: untuned)
 size_t bk_ntt_words();
 
+// Tensor-core path (exact fp16 limbs on tcgen05.mma kind::f16).
+size_t bk_tc_bytes();                                     // expanded Hankel key, fp16 limbs
+int prepare_bk_tc(const uint32_t *bk, void *bk_tc, cudaStream_t st);
+size_t tc_scratch_bytes(int njobs);                       // ACC, digits and inputs of a launch of njobs
+int configure_br_tc();
+int launch_br_tc(const BrJob *jobs, int njobs, const void *bk_tc, void *scratch, uint32_t *big, int *err,
+                 cudaStream_t st);
+
 int configure_key_switch();
 int launch_key_switch(const KsJob *jobs, int njobs, const uint32_t *big, const uint32_t *ksk_dev, int *err,
                       cudaStream_t st);
 int launch_free(const FreeJob *jobs, int njobs, cudaStream_t st);
+int launch_sum(const SumJob *jobs, int njobs, cudaStream_t st);
+int launch_trace(const TraceJob *jobs, int njobs, uint32_t *records, cudaStream_t st);
 int launch_pad_ksk(const uint32_t *ksk_abi, uint32_t *ksk_dev, cudaStream_t st);
 int launch_wait_selftest(int *err, cudaStream_t st);   // a bounded wait that is never satisfied
 

@@ -1,14 +1,18 @@
 """Serving benchmark: mixed-mode queries with Poisson arrivals through the
-continuous-batching loop (velopir_submit / velopir_progress).
+continuous-batching loop (velopir_submit / velopir_progress), with the
+library's issue thread stepping the loop (velopir_serve_start) so the GPU
+does not wait for the caller.
 
 Mix (shaped like the paper's three modes): 40% interval validation with D
 log-uniform in [256, 4096], 30% coordinate validation with D in [256, 16384],
-30% identifier matching (32-bit ids, 32-bit payload aggregation) with D in
-[1024, 65536].  Capacity is measured closed-loop (all queries submitted at
-once); then each load point replays Poisson arrivals at a multiple of that
-capacity and reports query latency p50/p99 (arrival to completion).
+30% identifier matching (32-bit ids, 32-bit payload aggregation, fan-in
+--fanin) with D in [1024, 65536].  Capacity is measured closed-loop (all
+queries submitted at once); then each load point replays Poisson arrivals at
+a multiple of that capacity and reports query latency p50/p99 (arrival to
+completion) over its queries after the first --warmup of the point, with the
+achieved against the offered rate.
 
-    python -m paper_2506_12761_gb300.serve_bench --per-point 10 --loads 0.5,1.0,1.5
+    python -m paper_2506_12761_gb300.serve_bench --per-point 60 --loads 0.25,0.5,0.75,1.0,1.25,1.5
 """
 from __future__ import annotations
 
@@ -22,7 +26,16 @@ from . import build, synth
 from . import velopir as vp
 
 
-def make_query(s, q: int, seed: int):
+def fanin_nodes(D: int, g: int) -> int:
+    """Bootstraps per payload bit of the XOR aggregation tree of fan-in g."""
+    nodes, k = 0, 1
+    while k < D:
+        nodes += sum(1 for i in range(0, D, g * k) if sum(1 for m in range(g) if i + m * k < D) >= 2)
+        k *= g
+    return nodes
+
+
+def make_query(s, q: int, seed: int, fanin: int = 2):
     st = synth.Stream(seed, synth.STREAM_ARRIVALS, 1000 + q)
     u = float(st.unit_doubles(1)[0])
     kind = 0 if u < 0.4 else (1 if u < 0.7 else 2)
@@ -46,18 +59,21 @@ def make_query(s, q: int, seed: int):
     a = vp.velopir_client_encrypt_bits(s, synth.value_bits([w["query"]], 32)[0], synth.lwe_material(32, seed=seed, substream=4000 + 2 * q))
     pay = w["payload"].astype(np.uint32)
     return dict(kind=vp.VP_QUERY_IDM, a=a, db=w["ids"].astype(np.uint32), D=D, id_bits=32, payload=pay,
-                payload_bits=32, out=np.zeros((32, 631), np.uint32),
-                want=synth.value_bits([int(pay[w["planted"]])], 32)[0], boots=31 * D + 32 * (D - 1))
+                payload_bits=32, out=np.zeros((32, 631), np.uint32), fanin=fanin,
+                want=synth.value_bits([int(pay[w["planted"]])], 32)[0], boots=31 * D + 32 * fanin_nodes(D, fanin))
 
 
 def record(q):
     return vp.make_query(q["kind"], q["a"], q["db"], q["D"], q["out"], enc_b=q.get("b"), id_bits=q.get("id_bits", 0),
-                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0))
+                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0),
+                         agg_fanin=q.get("fanin", 0))
 
 
-def run(ctx, queries, arrivals):
-    """Submit each query at its arrival time (seconds from start); step the
-    loop whenever work is in flight.  Returns per-query latency (s) and wall time."""
+def run(ctx, queries, arrivals, threaded: bool):
+    """Submit each query at its arrival time (seconds from start).  With the
+    issue thread the caller only submits and collects; otherwise it steps the
+    loop itself whenever work is in flight.  Returns per-query completion
+    times (s from start) and the wall time."""
     n = len(queries)
     recs = [record(q) for q in queries]
     t0 = time.perf_counter()
@@ -67,6 +83,11 @@ def run(ctx, queries, arrivals):
         while nxt < n and arrivals[nxt] <= now:
             ticket_of[vp.velopir_submit(ctx, recs[nxt])] = nxt
             nxt += 1
+        if threaded:
+            for t in vp.velopir_progress(ctx):
+                done_at[ticket_of[t]] = time.perf_counter() - t0
+            time.sleep(0.002 if nxt >= n else max(0.0, min(0.002, arrivals[nxt] - now)))
+            continue
         adm, wait = vp.velopir_queue_depth(ctx)
         if adm or wait:
             for t in vp.velopir_progress(ctx):
@@ -74,8 +95,7 @@ def run(ctx, queries, arrivals):
         elif nxt < n:
             time.sleep(max(0.0, min(0.05, arrivals[nxt] - now)))
     wall = time.perf_counter() - t0
-    lat = np.array([done_at[i] - arrivals[i] for i in range(n)])
-    return lat, wall
+    return np.array([done_at[i] for i in range(n)]), wall
 
 
 def check(s, queries):
@@ -89,9 +109,12 @@ def check(s, queries):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--per-point", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=0, help="queries at the start of each point left out of p50/p99")
     ap.add_argument("--capacity-queries", type=int, default=8)
     ap.add_argument("--loads", default="0.5,1.0,1.5")
     ap.add_argument("--budget-gb", type=float, default=96.0)
+    ap.add_argument("--fanin", type=int, default=8, help="IdM aggregation fan-in (2: the pairwise HomSum)")
+    ap.add_argument("--no-thread", action="store_true", help="step the loop from the caller (no issue thread)")
     ap.add_argument("--seed", type=int, default=synth.MASTER_SEED)
     args = ap.parse_args()
     build.build()
@@ -100,28 +123,44 @@ def main():
     ctx = vp.Context(0, int(args.budget_gb * (1 << 30)))
     vp.velopir_load_cloud_key(ctx.h, bk, ksk)
     vp.velopir_autotune(ctx.h)
+    threaded = not args.no_thread
+    if threaded:
+        vp.velopir_serve_start(ctx.h)
     # closed loop: every query at t = 0
-    cap_q = [make_query(km.s, q, args.seed) for q in range(args.capacity_queries)]
-    lat, wall = run(ctx.h, cap_q, np.zeros(len(cap_q)))
+    cap_q = [make_query(km.s, q, args.seed, args.fanin) for q in range(args.capacity_queries)]
+    done, wall = run(ctx.h, cap_q, np.zeros(len(cap_q)), threaded)
     capacity = len(cap_q) / wall
     boots = sum(q["boots"] for q in cap_q)
     result = {"metric": "query latency p50/p99 (ms) and throughput under Poisson load, mixed IntV/CoV/IdM",
+              "issue_thread": threaded, "idm_aggregation_fanin": args.fanin,
               "capacity": {"queries_per_s": capacity, "bootstraps_per_s": boots / wall, "queries": len(cap_q),
-                           "correct": check(km.s, cap_q)},
+                           "seconds": wall, "correct": check(km.s, cap_q)},
               "points": []}
+    print(json.dumps(result["capacity"]), flush=True)
     base = args.capacity_queries
     for li, load in enumerate(float(x) for x in args.loads.split(",")):
-        qs = [make_query(km.s, base + q, args.seed) for q in range(args.per_point)]
+        qs = [make_query(km.s, base + q, args.seed, args.fanin) for q in range(args.per_point)]
         base += args.per_point
         arr = synth.poisson_arrivals(len(qs), load * capacity, seed=args.seed, substream=li)
         arr = arr - arr[0]
-        lat, wall = run(ctx.h, qs, arr)
-        result["points"].append({"offered_load": load, "rate_qps": load * capacity, "queries": len(qs),
-                                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                                 "achieved_qps": len(qs) / wall,
-                                 "bootstraps_per_s": sum(q["boots"] for q in qs) / wall,
+        done, wall = run(ctx.h, qs, arr, threaded)
+        lat = done - arr
+        k = min(args.warmup, len(qs) - 1)
+        span = float(done[k:].max() - arr[k])          # first counted arrival to last completion
+        kinds = {0: "intv", 1: "cov", 2: "idm"}
+        per_mode = {kinds[m]: float(np.percentile(lat[k:][[q["kind"] == m for q in qs[k:]]], 50) * 1e3)
+                    for m in kinds if any(q["kind"] == m for q in qs[k:])}
+        result["points"].append({"offered_load": load, "offered_qps": load * capacity,
+                                 "queries": len(qs), "counted": len(qs) - k,
+                                 "p50_ms": float(np.percentile(lat[k:], 50) * 1e3),
+                                 "p99_ms": float(np.percentile(lat[k:], 99) * 1e3),
+                                 "p50_ms_by_mode": per_mode,
+                                 "achieved_qps": (len(qs) - k) / span,
+                                 "bootstraps_per_s": sum(q["boots"] for q in qs[k:]) / span,
                                  "correct": check(km.s, qs)})
         print(json.dumps(result["points"][-1]), flush=True)
+    if threaded:
+        vp.velopir_serve_stop(ctx.h)
     print(json.dumps(result), flush=True)
     ctx.close()
 

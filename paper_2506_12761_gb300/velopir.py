@@ -1,4 +1,6 @@
-"""Thin ctypes binding of libvelopir.so (include/velopir.h), same names.
+"""Thin ctypes binding of libvelopir.so (include/velopir.h) and of the
+host-only client library libvelopir_client.so (include/velopir_client.h),
+same names.
 
 Argument marshalling only: every step of gate bootstrapping and of the mode
 circuits runs in the library's CUDA kernels.  Buffers may be numpy arrays
@@ -15,6 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "libvelopir.so")
+CLIENT_LIB = os.path.join(HERE, "libvelopir_client.so")
 
 VELOPIR_OK = 0
 ERRORS = {-1: "ERR_ARG", -2: "ERR_NOKEY", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_TIMEOUT", -6: "ERR_BUSY",
@@ -28,22 +31,34 @@ LWE_WORDS = 631
 BK_WORDS = 630 * 6 * 2 * 1024
 KSK_WORDS = 1024 * 8 * 4 * 631
 
-# Every symbol include/velopir.h declares.
+# Every symbol include/velopir.h declares (the GPU library).
 EXPORTS = [
     "velopir_create", "velopir_destroy", "velopir_load_cloud_key", "velopir_set_path",
     "velopir_bootstrap_batch", "velopir_bootstrap_plain", "velopir_interval_query",
     "velopir_coordinate_query", "velopir_id_match", "velopir_submit", "velopir_poll",
     "velopir_queue_depth", "velopir_sync", "velopir_last_error", "velopir_launch_count",
-    "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
     "velopir_profile", "velopir_profile_read", "velopir_query_batch", "velopir_graph_replays",
     "velopir_bootstrap_batch_noalloc", "velopir_autotune", "velopir_tuned_shape", "velopir_progress",
-    "velopir_selftest_wait_timeout", "velopir_plan_query", "velopir_client_pubkeygen", "velopir_server_encrypt",
+    "velopir_selftest_wait_timeout", "velopir_plan_query",
     "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb", "velopir_cancel",
-    "velopir_plan_batch",
+    "velopir_plan_batch", "velopir_trace_start", "velopir_trace_stop", "velopir_set_launch_limit",
+    "velopir_serve_start", "velopir_serve_stop",
+]
+# Every symbol include/velopir_client.h declares (the host-only client library).
+CLIENT_EXPORTS = [
+    "velopir_client_keygen", "velopir_client_encrypt_bits", "velopir_client_decrypt_bits",
+    "velopir_client_pubkeygen", "velopir_server_encrypt",
 ]
 NOALLOC_MAX_GATES = 256
 NTT_TILE_SHAPES = (6, 8, 9, 10, 12)
-VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE = 0, 1, 2
+VP_KERNEL_BLIND_ROTATE, VP_KERNEL_KEY_SWITCH, VP_KERNEL_FREE, VP_KERNEL_SUM, VP_KERNEL_TRACE = 0, 1, 2, 3, 4
+MAX_FANIN = 8
+TRACE_MAX_IN = 8
+# velopir_trace_rec
+TRACE_DTYPE = np.dtype([("nrot", "<u4"), ("nin", "<u4"), ("ks_cst", "<u4"), ("cst", "<u4", (2,)),
+                        ("coef", "<i4", (2, TRACE_MAX_IN)), ("inp", "<u4", (TRACE_MAX_IN, LWE_WORDS)),
+                        ("out", "<u4", (LWE_WORDS,))])
+assert TRACE_DTYPE.itemsize == 22800
 
 
 class VelopirError(RuntimeError):
@@ -62,12 +77,36 @@ def paper_params() -> Params:
 
 class Query(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("id_bits", ctypes.c_int32), ("payload_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("enc_a", ctypes.c_void_p), ("enc_b", ctypes.c_void_p),
+                ("agg_fanin", ctypes.c_int32), ("enc_a", ctypes.c_void_p), ("enc_b", ctypes.c_void_p),
                 ("db", ctypes.c_void_p), ("payload", ctypes.c_void_p), ("D", ctypes.c_size_t),
                 ("out", ctypes.c_void_p)]
 
 
 _lib = None
+_clib = None
+
+
+def clib() -> ctypes.CDLL:
+    """The host-only client library (no CUDA runtime is loaded)."""
+    global _clib
+    if _clib is None:
+        if not os.path.exists(CLIENT_LIB):
+            raise ImportError(f"{CLIENT_LIB} is missing: build it with paper_2506_12761_gb300.build.build()")
+        L = ctypes.CDLL(CLIENT_LIB)
+        vp, sz, i = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        sig = {
+            "velopir_client_keygen": (i, [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+            "velopir_client_encrypt_bits": (i, [vp, vp, vp, vp, sz, vp]),
+            "velopir_client_decrypt_bits": (i, [vp, vp, sz, vp]),
+            "velopir_client_pubkeygen": (i, [vp, vp, vp, sz, vp]),
+            "velopir_server_encrypt": (i, [vp, vp, sz, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _clib = L
+    return _clib
 
 
 def lib() -> ctypes.CDLL:
@@ -82,6 +121,9 @@ def lib() -> ctypes.CDLL:
             "velopir_destroy": (i, [vp]),
             "velopir_load_cloud_key": (i, [vp, ctypes.POINTER(Params), vp, sz, vp, sz]),
             "velopir_set_path": (i, [vp, i]),
+            "velopir_set_launch_limit": (i, [vp, sz]),
+            "velopir_serve_start": (i, [vp]),
+            "velopir_serve_stop": (i, [vp]),
             "velopir_bootstrap_batch": (i, [vp, i, vp, vp, sz]),
             "velopir_bootstrap_plain": (i, [vp, i, vp, vp, sz]),
             "velopir_bootstrap_batch_noalloc": (i, [vp, i, vp, vp, sz]),
@@ -97,9 +139,6 @@ def lib() -> ctypes.CDLL:
             "velopir_last_error": (ctypes.c_char_p, [vp]),
             "velopir_launch_count": (u64, [vp]),
             "velopir_selftest_wait_timeout": (i, [vp]),
-            "velopir_client_keygen": (i, [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
-            "velopir_client_encrypt_bits": (i, [vp, vp, vp, vp, sz, vp]),
-            "velopir_client_decrypt_bits": (i, [vp, vp, sz, vp]),
             "velopir_profile": (i, [vp, i]),
             "velopir_query_batch": (i, [vp, ctypes.POINTER(Query), sz, i]),
             "velopir_graph_replays": (u64, [vp]),
@@ -107,13 +146,13 @@ def lib() -> ctypes.CDLL:
             "velopir_tuned_shape": (i, [vp, sz]),
             "velopir_plan_query": (i, [ctypes.POINTER(Query), i, vp, vp, vp, ctypes.POINTER(sz), i]),
             "velopir_plan_batch": (i, [ctypes.POINTER(Query), sz, i, i, vp, vp, vp, ctypes.POINTER(sz), i]),
-            "velopir_client_pubkeygen": (i, [vp, vp, vp, sz, vp]),
-            "velopir_server_encrypt": (i, [vp, vp, sz, vp]),
             "velopir_interval_query_encdb": (i, [vp, vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_coordinate_query_encdb": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_id_match_encdb": (i, [vp, vp, i, vp, sz, vp, i, vp]),
             "velopir_profile_read": (i, [vp, i, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                          ctypes.POINTER(ctypes.c_double)]),
+            "velopir_trace_start": (i, [vp, u64, ctypes.c_uint32, ctypes.c_uint32, sz]),
+            "velopir_trace_stop": (i, [vp, vp, sz, ctypes.POINTER(sz)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -140,6 +179,11 @@ def _check(ctx, rc: int):
         raise VelopirError(rc, msg.decode() if msg else "")
 
 
+def _check_client(rc: int):
+    if rc != VELOPIR_OK:
+        raise VelopirError(rc, "invalid argument to the client library")
+
+
 # ---- the C ABI, one function each -----------------------------------------
 
 def velopir_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int | None = None):
@@ -160,6 +204,11 @@ def velopir_load_cloud_key(ctx, bk, ksk, params: Params | None = None) -> None:
 
 def velopir_set_path(ctx, path: int) -> None:
     _check(ctx, lib().velopir_set_path(ctx, path))
+
+
+def velopir_set_launch_limit(ctx, max_rotations: int) -> None:
+    """Blind rotations per launch at most (1: one bootstrap per launch; 0: default)."""
+    _check(ctx, lib().velopir_set_launch_limit(ctx, max_rotations))
 
 
 def velopir_bootstrap_batch(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:
@@ -211,10 +260,10 @@ def velopir_tuned_shape(ctx, count: int) -> int:
 
 
 def make_query(kind: int, enc_a, db, D: int, out, enc_b=None, id_bits: int = 0, payload=None,
-               payload_bits: int = 0) -> Query:
+               payload_bits: int = 0, agg_fanin: int = 0) -> Query:
     """A velopir_query record; the caller keeps every buffer alive until the query finishes."""
-    return Query(kind, id_bits, payload_bits if payload is not None else 0, 0, ptr(enc_a), ptr(enc_b), ptr(db),
-                 ptr(payload), D, ptr(out))
+    return Query(kind, id_bits, payload_bits if payload is not None else 0, agg_fanin, ptr(enc_a), ptr(enc_b),
+                 ptr(db), ptr(payload), D, ptr(out))
 
 
 def velopir_submit(ctx, query: Query) -> int:
@@ -239,6 +288,15 @@ def velopir_progress(ctx, cap: int = 256) -> list[int]:
     n = ctypes.c_size_t()
     _check(ctx, lib().velopir_progress(ctx, buf, cap, ctypes.byref(n)))
     return [int(buf[i]) for i in range(n.value)]
+
+
+def velopir_serve_start(ctx) -> None:
+    """Start the library's issue thread (serving steps back to back)."""
+    _check(ctx, lib().velopir_serve_start(ctx))
+
+
+def velopir_serve_stop(ctx) -> None:
+    _check(ctx, lib().velopir_serve_stop(ctx))
 
 
 def velopir_queue_depth(ctx) -> tuple[int, int]:
@@ -276,15 +334,28 @@ def velopir_profile_read(ctx, kernel: int) -> tuple[int, int, float]:
     return n.value, u.value, ms.value
 
 
+def velopir_trace_start(ctx, seed: int, per_launch: int, one_in: int, cap: int) -> None:
+    """Record max(min(per_launch, G), ceil(G / one_in)) sampled gates of every launch of G, at most cap in all."""
+    _check(ctx, lib().velopir_trace_start(ctx, seed, per_launch, one_in, cap))
+
+
+def velopir_trace_stop(ctx, cap: int) -> np.ndarray:
+    """Stop tracing; the first min(cap, recorded) records as a TRACE_DTYPE array."""
+    n = ctypes.c_size_t()
+    out = np.zeros(max(1, cap), dtype=TRACE_DTYPE)
+    _check(ctx, lib().velopir_trace_stop(ctx, out.ctypes.data if cap else None, cap, ctypes.byref(n)))
+    return out[: min(cap, n.value)]
+
+
 def velopir_client_keygen(km, params: Params | None = None):
     """Cloud key (bk, ksk) as numpy arrays from synth.KeyMaterial."""
     p = params or paper_params()
     c = {k: np.ascontiguousarray(getattr(km, k), dtype=np.uint32) for k in ("s", "K", "bk_a", "bk_e", "ksk_a", "ksk_e")}
     bk = np.empty(BK_WORDS, dtype=np.uint32)
     ksk = np.empty(KSK_WORDS, dtype=np.uint32)
-    rc = lib().velopir_client_keygen(ctypes.byref(p), ptr(c["s"]), ptr(c["K"]), ptr(c["bk_a"]), ptr(c["bk_e"]),
+    rc = clib().velopir_client_keygen(ctypes.byref(p), ptr(c["s"]), ptr(c["K"]), ptr(c["bk_a"]), ptr(c["bk_e"]),
                                      ptr(c["ksk_a"]), ptr(c["ksk_e"]), ptr(bk), ptr(ksk))
-    _check(None, rc)
+    _check_client(rc)
     return bk, ksk
 
 
@@ -294,7 +365,7 @@ def velopir_client_encrypt_bits(s, bits, lwe_mat) -> np.ndarray:
     a = np.ascontiguousarray(lwe_mat.a[:n], dtype=np.uint32)
     e = np.ascontiguousarray(lwe_mat.e[:n], dtype=np.uint32)
     out = np.empty((n, LWE_WORDS), dtype=np.uint32)
-    _check(None, lib().velopir_client_encrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(bits),
+    _check_client(clib().velopir_client_encrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(bits),
                                                    ptr(a), ptr(e), n, ptr(out)))
     return out
 
@@ -302,7 +373,7 @@ def velopir_client_encrypt_bits(s, bits, lwe_mat) -> np.ndarray:
 def velopir_client_decrypt_bits(s, ct) -> np.ndarray:
     ct = np.ascontiguousarray(np.asarray(ct, dtype=np.uint32).reshape(-1, LWE_WORDS))
     out = np.empty(ct.shape[0], dtype=np.uint32)
-    _check(None, lib().velopir_client_decrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(ct),
+    _check_client(clib().velopir_client_decrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(ct),
                                                    ct.shape[0], ptr(out)))
     return out
 
@@ -332,7 +403,7 @@ class Context:
 
 
 def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0, id_bits: int = 0,
-                       payload=None, payload_bits: int = 0, max_launches: int = 4096):
+                       payload=None, payload_bits: int = 0, max_launches: int = 4096, agg_fanin: int = 0):
     """Host-only dry run of a query's launch plan on plaintext bits.  For the
     VP_PLAN_*_ENCDB kinds id_bits is the width (l, w or id_bits) and db /
     payload are plaintext values the dry run encrypts.
@@ -344,7 +415,7 @@ def velopir_plan_query(kind: int, db, D: int, bits_a, bits_b=None, wave: int = 0
     a = np.ascontiguousarray(bits_a, dtype=np.uint32)
     b = None if bits_b is None else np.ascontiguousarray(bits_b, dtype=np.uint32)
     pay = None if payload is None else np.ascontiguousarray(payload, dtype=np.uint32)
-    q = Query(kind, id_bits, payload_bits, 0, None, None, ptr(db), ptr(pay), D, None)
+    q = Query(kind, id_bits, payload_bits, agg_fanin, None, None, ptr(db), ptr(pay), D, None)
     nout = payload_bits if payload is not None else D
     out = np.zeros(max(1, nout), dtype=np.uint32)
     sizes = (ctypes.c_size_t * max_launches)()
@@ -361,7 +432,7 @@ def velopir_client_pubkeygen(s, lwe_mat_zero) -> np.ndarray:
     e = np.ascontiguousarray(lwe_mat_zero.e, dtype=np.uint32)
     count = e.shape[0]
     out = np.zeros((count, LWE_WORDS), dtype=np.uint32)
-    _check(None, lib().velopir_client_pubkeygen(ptr(s), ptr(a), ptr(e), count, ptr(out)))
+    _check_client(clib().velopir_client_pubkeygen(ptr(s), ptr(a), ptr(e), count, ptr(out)))
     return out
 
 
@@ -371,7 +442,7 @@ def velopir_server_encrypt(pk, bits) -> np.ndarray:
     b = np.ascontiguousarray(bits, dtype=np.uint32).reshape(-1)
     assert pk.shape[0] == b.shape[0]
     out = np.zeros_like(pk)
-    _check(None, lib().velopir_server_encrypt(ptr(pk), ptr(b), b.shape[0], ptr(out)))
+    _check_client(clib().velopir_server_encrypt(ptr(pk), ptr(b), b.shape[0], ptr(out)))
     return out.reshape(np.shape(bits) + (LWE_WORDS,))
 
 
@@ -402,8 +473,8 @@ def velopir_plan_batch(queries, wave: int = 0, chunk_rows: int = 0, max_launches
         db = np.ascontiguousarray(q["db"], dtype=np.uint32)
         pay = None if q.get("payload") is None else np.ascontiguousarray(q["payload"], dtype=np.uint32)
         keep += [db, pay]
-        recs.append(Query(q["kind"], q.get("id_bits", 0), q.get("payload_bits", 0) if pay is not None else 0, 0,
-                          None, None, ptr(db), ptr(pay), q["D"], None))
+        recs.append(Query(q["kind"], q.get("id_bits", 0), q.get("payload_bits", 0) if pay is not None else 0,
+                          q.get("agg_fanin", 0), None, None, ptr(db), ptr(pay), q["D"], None))
         a.append(np.asarray(q["bits_a"], dtype=np.uint32))
         if q["kind"] == VP_QUERY_INTV:
             b.append(np.asarray(q["bits_b"], dtype=np.uint32))

@@ -1,8 +1,12 @@
-"""The C-ABI library loads, exports every symbol include/velopir.h declares,
-and its host-only client functions agree bit for bit with the oracle."""
+"""The two C-ABI libraries load and export every symbol their headers
+declare: libvelopir.so (include/velopir.h, the GPU library) and
+libvelopir_client.so (include/velopir_client.h, host only: it links no CUDA
+library); the client functions agree bit for bit with the oracle."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -19,8 +23,14 @@ def lib():
     return vp.lib()
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "velopir.h")).read()
+@pytest.fixture(scope="module")
+def clib():
+    build.build()
+    return vp.clib()
+
+
+def declared_symbols(header="velopir.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(velopir_[a-z_]+)\s*\(", src)))
 
@@ -31,6 +41,35 @@ def test_exports_every_declared_symbol(lib):
     for name in decl:
         assert hasattr(lib, name), name
     assert sorted(vp.EXPORTS) == decl
+
+
+def test_client_library_exports_its_header_and_the_gpu_library_does_not(lib, clib):
+    decl = declared_symbols("velopir_client.h")
+    assert sorted(vp.CLIENT_EXPORTS) == decl and len(decl) == 5
+    for name in decl:
+        assert hasattr(clib, name), name
+    gpu = ctypes.CDLL(build.LIB)
+    for name in decl:
+        assert not hasattr(gpu, name), f"{name} is exported by the GPU library"
+    assert not set(decl) & set(declared_symbols())
+
+
+def test_client_library_needs_no_cuda(clib):
+    """Its dynamic dependencies name no CUDA library, and a fresh interpreter
+    that loads it and encrypts and decrypts has no CUDA library mapped."""
+    if shutil.which("ldd"):
+        deps = subprocess.run(["ldd", build.CLIENT_LIB], capture_output=True, text=True).stdout
+        assert "cuda" not in deps.lower(), deps
+    code = ("import ctypes, numpy as np; L = ctypes.CDLL(%r); "
+            "s = np.zeros(630, np.uint32); a = np.zeros(630, np.uint32); e = np.zeros(1, np.uint32); "
+            "b = np.ones(1, np.uint32); ct = np.zeros(631, np.uint32); o = np.zeros(1, np.uint32); "
+            "p = lambda x: x.ctypes.data_as(ctypes.c_void_p); "
+            "assert L.velopir_client_encrypt_bits(p(s), p(b), p(a), p(e), ctypes.c_size_t(1), p(ct)) == 0; "
+            "assert L.velopir_client_decrypt_bits(p(s), p(ct), ctypes.c_size_t(1), p(o)) == 0 and o[0] == 1; "
+            "maps = open('/proc/self/maps').read(); assert 'libcuda' not in maps, 'CUDA mapped'; print('ok')"
+            ) % build.CLIENT_LIB
+    r = subprocess.run(["python3", "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
 
 
 def test_create_without_gpu_fails_cleanly(lib):
@@ -68,7 +107,7 @@ def test_client_encrypt_decrypt_matches_oracle(lib, paper_keys):
     assert np.array_equal(vp.velopir_client_decrypt_bits(paper_keys.s, ct), oracle.decrypt_bits(paper_keys.s, ct))
 
 
-def test_client_rejects_other_parameters(lib):
+def test_client_rejects_other_parameters(clib):
     p = vp.Params(500, 1024, 1, 3, 7, 8, 2)
     z = np.zeros(16, dtype=np.uint32)
-    assert lib.velopir_client_keygen(ctypes.byref(p), *(vp.ptr(z),) * 8) == -1
+    assert clib.velopir_client_keygen(ctypes.byref(p), *(vp.ptr(z),) * 8) == -1

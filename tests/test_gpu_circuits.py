@@ -91,3 +91,27 @@ def test_device_resident_database(paper_keys):
     vp.velopir_interval_query(ctx.h, dx, dy, dr, 2, dout)
     out = dout.cpu().numpy().view(np.uint32)
     assert np.array_equal(out, oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
+
+
+def test_launch_limit_one_is_one_bootstrap_per_launch(paper_keys):
+    """velopir_set_launch_limit(1): every blind-rotation launch holds one
+    gate (the plain baseline of a whole query); the ciphertexts equal the
+    layer-batched ones and the oracle's."""
+    ctx, s = gpu_ctx()
+    w = synth.idm_workload(4, 8)
+    x = encrypt_value_bits(s, w["query"], 8, 507)
+    ids = w["ids"].astype(np.uint32)
+    batched = np.zeros((4, 631), dtype=np.uint32)
+    vp.velopir_id_match(ctx.h, x, 8, ids, 4, None, 0, batched)
+    plain = np.zeros_like(batched)
+    vp.velopir_set_launch_limit(ctx.h, 1)
+    try:
+        vp.velopir_profile(ctx.h, True)
+        vp.velopir_id_match(ctx.h, x, 8, ids, 4, None, 0, plain)
+        launches, rotations, _ = vp.velopir_profile_read(ctx.h, vp.VP_KERNEL_BLIND_ROTATE)
+        vp.velopir_profile(ctx.h, False)
+    finally:
+        vp.velopir_set_launch_limit(ctx.h, 0)
+    assert rotations == 28 and launches == 28
+    assert np.array_equal(plain, batched)
+    assert np.array_equal(plain, oracle.idm_batch(paper_keys, x, ids))

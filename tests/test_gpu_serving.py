@@ -1,19 +1,21 @@
 """Multi-query batches (one merged program, optional CUDA-graph replay) and the
-continuous-batching serving loop: every result is bit-identical to the same
-query run alone, and to the oracle."""
+continuous-batching serving loop: every result is bit-identical to the
+oracle's circuit on the query's own ciphertexts, and to the same query run
+alone."""
 import numpy as np
 import pytest
 
 import oracle
-from gpu_common import encrypt_value_bits, gpu_ctx
+from gpu_common import check_trace, encrypt_value_bits, gpu_ctx
 from paper_2506_12761_gb300 import synth
 from paper_2506_12761_gb300 import velopir as vp
 
 pytestmark = pytest.mark.gpu
 
 
-def make_queries(s, seed):
-    """IntV D=2, CoV D=3, IdM-8 D=4 with payload: three modes, uneven sizes."""
+def make_queries(s, seed, fanin=0):
+    """IntV D=2, CoV D=3, IdM-8 D=4 with payload (aggregated pairwise, or with
+    fan-in `fanin`): three modes, uneven sizes."""
     qs = []
     w = synth.intv_workload(2, substream=seed)
     cx, cy = encrypt_value_bits(s, w["x"], 32, 900 + seed), encrypt_value_bits(s, w["y"], 32, 901 + seed)
@@ -25,13 +27,44 @@ def make_queries(s, seed):
     w = synth.idm_workload(4, 8, payload=True, substream=seed + 2)
     x = encrypt_value_bits(s, w["query"], 8, 903 + seed)
     qs.append(dict(kind=vp.VP_QUERY_IDM, a=x, db=w["ids"].astype(np.uint32), D=4, id_bits=8,
-                   payload=w["payload"].astype(np.uint32), payload_bits=32, out=np.zeros((32, 631), np.uint32)))
+                   payload=w["payload"].astype(np.uint32), payload_bits=32, out=np.zeros((32, 631), np.uint32),
+                   fanin=fanin))
     return qs
 
 
 def as_record(q):
     return vp.make_query(q["kind"], q["a"], q["db"], q["D"], q["out"], enc_b=q.get("b"), id_bits=q.get("id_bits", 0),
-                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0))
+                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0), agg_fanin=q.get("fanin", 0))
+
+
+def _oracle_circuit(keys, q):
+    if q["kind"] == vp.VP_QUERY_INTV:
+        return oracle.intv_batch(keys, q["a"], q["b"], q["db"].astype(np.uint64))
+    if q["kind"] == vp.VP_QUERY_COV:
+        return oracle.cov_batch(keys, q["a"], q["db"])
+    return oracle.idm_payload(keys, q["a"], q["db"], q["payload"], q["payload_bits"], fanin=max(2, q.get("fanin", 0)))
+
+
+_ORACLE = {}
+
+
+def oracle_out(keys, q):
+    """The oracle's circuit for one query, from the query's own ciphertexts.
+    The serving tests share two query sets (make_queries seeds 3 and 4); their
+    oracle outputs are computed once, all six circuits at a time."""
+    key = (q["kind"], q["a"].tobytes(), q.get("fanin", 0))
+    if key not in _ORACLE:
+        from concurrent.futures import ThreadPoolExecutor
+        _, s = gpu_ctx()
+        todo = [x for x in make_queries(s, 3) + make_queries(s, 4, fanin=4)
+                if (x["kind"], x["a"].tobytes(), x.get("fanin", 0)) not in _ORACLE]
+        if not any((x["kind"], x["a"].tobytes(), x.get("fanin", 0)) == key for x in todo):
+            todo.append(q)
+        with ThreadPoolExecutor(len(todo)) as ex:
+            outs = list(ex.map(lambda x: _oracle_circuit(keys, x), todo))
+        for x, o in zip(todo, outs):
+            _ORACLE[(x["kind"], x["a"].tobytes(), x.get("fanin", 0))] = o
+    return _ORACLE[key]
 
 
 def run_alone(ctx, q):
@@ -40,6 +73,10 @@ def run_alone(ctx, q):
         vp.velopir_interval_query(ctx.h, q["a"], q["b"], q["db"], q["D"], out)
     elif q["kind"] == vp.VP_QUERY_COV:
         vp.velopir_coordinate_query(ctx.h, q["a"], q["db"], q["D"], out)
+    elif q.get("fanin", 0):
+        vp.velopir_query_batch(ctx.h, [vp.make_query(q["kind"], q["a"], q["db"], q["D"], out, id_bits=q["id_bits"],
+                                                     payload=q["payload"], payload_bits=q["payload_bits"],
+                                                     agg_fanin=q["fanin"])])
     else:
         vp.velopir_id_match(ctx.h, q["a"], q["id_bits"], q["db"], q["D"], q["payload"], q["payload_bits"], out)
     return out
@@ -47,19 +84,17 @@ def run_alone(ctx, q):
 
 def test_query_batch_matches_alone_and_oracle(paper_keys):
     ctx, s = gpu_ctx()
-    qs = make_queries(s, 1)
+    qs = make_queries(s, 3)
     vp.velopir_query_batch(ctx.h, [as_record(q) for q in qs])
     for q in qs:
         assert np.array_equal(q["out"], run_alone(ctx, q))
-    intv, cov, idm = qs
-    assert np.array_equal(intv["out"], oracle.intv_batch(paper_keys, intv["a"], intv["b"], intv["db"].astype(np.uint64)))
-    assert np.array_equal(cov["out"], oracle.cov_batch(paper_keys, cov["a"], cov["db"]))
-    assert np.array_equal(idm["out"], oracle.idm_payload(paper_keys, idm["a"], idm["db"], idm["payload"], 32))
+    for q in qs:
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
 
 
-def test_query_batch_graph_replay():
+def test_query_batch_graph_replay(paper_keys):
     ctx, s = gpu_ctx()
-    qs = make_queries(s, 2)
+    qs = make_queries(s, 4, fanin=4)
     r0 = vp.velopir_graph_replays(ctx.h)
     vp.velopir_query_batch(ctx.h, [as_record(q) for q in qs], use_graph=True)
     first = [q["out"].copy() for q in qs]
@@ -69,15 +104,18 @@ def test_query_batch_graph_replay():
     assert vp.velopir_graph_replays(ctx.h) == r0 + 1
     for q, f in zip(qs, first):
         assert np.array_equal(q["out"], f)
-        assert np.array_equal(q["out"], run_alone(ctx, q))
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
 
 
-def test_serving_results_identical_alone_and_in_the_mix():
+def test_serving_results_identical_alone_and_in_the_mix(paper_keys):
     """Queries arriving while others are on the GPU are admitted into the
-    running layer batches; each result equals the query run alone."""
+    running layer batches; each result equals the oracle's circuit on the
+    query's inputs and the query run alone, and every traced gate of the
+    serving steps equals the oracle's."""
     ctx, s = gpu_ctx()
-    qs = make_queries(s, 3) + make_queries(s, 4)
+    qs = make_queries(s, 3) + make_queries(s, 4, fanin=4)
     alone = [run_alone(ctx, q) for q in qs]
+    vp.velopir_trace_start(ctx.h, 33, 4, 0, 4096)
     tickets = {}
     pending = list(range(len(qs)))
     done = set()
@@ -92,12 +130,15 @@ def test_serving_results_identical_alone_and_in_the_mix():
                 done.add(i)
         polls += 1
         assert polls < 500
+    recs = vp.velopir_trace_stop(ctx.h, 4096)
     for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
         assert np.array_equal(q["out"], a)
     assert vp.velopir_queue_depth(ctx.h) == (0, 0)
+    check_trace(paper_keys, recs, 64)
 
 
-def test_serving_admission_respects_memory_budget():
+def test_serving_admission_respects_memory_budget(paper_keys):
     """A context with a small HBM budget admits queries one at a time but still finishes them all."""
     _, s = gpu_ctx()
     from gpu_common import _state
@@ -105,7 +146,7 @@ def test_serving_admission_respects_memory_budget():
     bk, ksk = vp.velopir_client_keygen(km)
     ctx = vp.Context(0, hbm_budget_bytes=700 << 20)
     vp.velopir_load_cloud_key(ctx.h, bk, ksk)
-    qs = make_queries(s, 5)
+    qs = make_queries(s, 3)
     alone = [run_alone(_state["ctx"], q) for q in qs]
     ts = [vp.velopir_submit(ctx.h, as_record(q)) for q in qs]
     left = set(range(len(qs)))
@@ -117,6 +158,7 @@ def test_serving_admission_respects_memory_budget():
             break
     assert not left
     for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
         assert np.array_equal(q["out"], a)
     ctx.close()
 
@@ -130,11 +172,11 @@ def test_submit_errors():
         vp.velopir_poll(ctx.h, 10 ** 9)
 
 
-def test_progress_reports_every_ticket_once():
+def test_progress_reports_every_ticket_once(paper_keys):
     """velopir_progress steps the loop and reports each finished ticket once;
     results equal the queries run alone."""
     ctx, s = gpu_ctx()
-    qs = make_queries(s, 6)
+    qs = make_queries(s, 4, fanin=4)
     alone = [run_alone(ctx, q) for q in qs]
     tickets = {vp.velopir_submit(ctx.h, as_record(q)): i for i, q in enumerate(qs)}
     seen = []
@@ -145,15 +187,16 @@ def test_progress_reports_every_ticket_once():
     assert sorted(seen) == sorted(tickets)
     assert vp.velopir_progress(ctx.h) == []
     for q, a in zip(qs, alone):
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
         assert np.array_equal(q["out"], a)
 
 
-def test_cancel_waiting_and_admitted_queries():
+def test_cancel_waiting_and_admitted_queries(paper_keys):
     """A query cancelled before admission, or while its layers run, is
     reported once as cancelled (velopir_poll raises ERR_CANCELLED); the others
     finish with the results they have alone, and admitted memory is released."""
     ctx, s = gpu_ctx()
-    qs = make_queries(s, 7)            # IntV (34 layers), CoV, IdM
+    qs = make_queries(s, 3)            # IntV (34 layers), CoV, IdM
     alone = [run_alone(ctx, q) for q in qs]
     ts = [vp.velopir_submit(ctx.h, as_record(q)) for q in qs]
     vp.velopir_cancel(ctx.h, ts[1])    # still waiting: dropped at once
@@ -176,7 +219,40 @@ def test_cancel_waiting_and_admitted_queries():
         if len(done) + len(cancelled) == 2:
             break
     assert cancelled == {0} and done == {2}
+    assert np.array_equal(qs[2]["out"], oracle_out(paper_keys, qs[2]))
     assert np.array_equal(qs[2]["out"], alone[2])
     assert vp.velopir_queue_depth(ctx.h) == (0, 0)
     with pytest.raises(vp.VelopirError):
         vp.velopir_cancel(ctx.h, 10 ** 9)
+
+
+def test_issue_thread_serves_staggered_arrivals(paper_keys):
+    """With the library's issue thread running, queries submitted while
+    others are on the GPU finish without the caller stepping the loop; every
+    result equals the oracle's, and non-serving calls are refused until the
+    thread stops."""
+    import time
+    ctx, s = gpu_ctx()
+    qs = make_queries(s, 3) + make_queries(s, 4, fanin=4)
+    vp.velopir_serve_start(ctx.h)
+    try:
+        with pytest.raises(vp.VelopirError) as e:
+            vp.velopir_sync(ctx.h)
+        assert e.value.code == vp.ERRORS_BY_NAME["ERR_BUSY"]
+        tickets = {}
+        for i, q in enumerate(qs):
+            tickets[vp.velopir_submit(ctx.h, as_record(q))] = i
+            time.sleep(0.05)
+        seen = set()
+        t0 = time.time()
+        while len(seen) < len(qs):
+            seen.update(vp.velopir_progress(ctx.h))
+            time.sleep(0.01)
+            assert time.time() - t0 < 300
+        assert seen == set(tickets)
+    finally:
+        vp.velopir_serve_stop(ctx.h)
+    vp.velopir_sync(ctx.h)
+    for q in qs:
+        assert np.array_equal(q["out"], oracle_out(paper_keys, q))
+    assert vp.velopir_queue_depth(ctx.h) == (0, 0)

@@ -213,3 +213,60 @@ def test_batch_of_uneven_queries_in_chunked_launch_order():
         launches_are_waves(sizes, wave, sum(131 * q["D"] if q["kind"] == vp.VP_QUERY_INTV else
                                             31 * q["D"] if q["kind"] == vp.VP_QUERY_COV else
                                             19 * q["D"] + 32 * (q["D"] - 1) for q in qs))
+
+
+def fanin_nodes(D, g):
+    """Bootstraps per payload bit of the fan-in-g XOR tree (groups with >= 2 members)."""
+    nodes, k = 0, 1
+    while k < D:
+        for i in range(0, D, g * k):
+            if sum(1 for q in range(g) if i + q * k < D) >= 2:
+                nodes += 1
+        k *= g
+    return nodes
+
+
+@pytest.mark.parametrize("fanin", [2, 3, 4, 8])
+@pytest.mark.parametrize("wave", [0, 64, 1824])
+def test_idm_payload_fanin_tree_plan(fanin, wave):
+    """The fan-in-g XOR aggregation (one bootstrap of 2 sum c + T((g-1)/4) per
+    group) answers the planted entry's payload at ragged sizes, and costs
+    31 D + 32 nodes(D, g) bootstraps: (D - 1) / (g - 1) per bit when D is a
+    power of g."""
+    rng = np.random.default_rng(60 + fanin)
+    for D in (1, 2, fanin, fanin + 1, 77, fanin ** 3):
+        ids = rng.choice(2**32, size=D, replace=False).astype(np.uint32)
+        pay = rng.integers(0, 2**32, size=D, dtype=np.uint64).astype(np.uint32)
+        hit = D // 2
+        out, sizes = vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, D, bits(int(ids[hit]), 32), wave=wave, id_bits=32,
+                                           payload=pay, payload_bits=32, agg_fanin=fanin)
+        assert np.array_equal(out, bits(pay[hit], 32)), (D, fanin)
+        launches_are_waves(sizes, wave, 31 * D + 32 * fanin_nodes(D, fanin))
+    assert fanin_nodes(fanin ** 3, fanin) == (fanin ** 3 - 1) // (fanin - 1)
+
+
+def test_fanin_tree_in_chunked_batch_order():
+    """Several fan-in IdM queries (and a pairwise one) in one merged program,
+    wave-filled and split into small chunks: the sums of a layer run before
+    its rotations, and no slot is read after reuse."""
+    rng = np.random.default_rng(77)
+    qs, want = [], []
+    for k, (fanin, D) in enumerate(((8, 300), (4, 129), (3, 50), (0, 90))):
+        ids = rng.choice(1 << 20, size=D, replace=False).astype(np.uint32)
+        pay = rng.integers(0, 1 << 32, size=D, dtype=np.uint64).astype(np.uint32)
+        hit = int(rng.integers(0, D))
+        qs.append(dict(kind=vp.VP_QUERY_IDM, db=ids, D=D, bits_a=bits(int(ids[hit]), 20), id_bits=20,
+                       payload=pay, payload_bits=32, agg_fanin=fanin))
+        want.append(bits(int(pay[hit]), 32))
+    for wave, chunk in ((0, 0), (96, 37), (1824, 200)):
+        outs, _ = vp.velopir_plan_batch(qs, wave=wave, chunk_rows=chunk)
+        for o, w in zip(outs, want):
+            assert np.array_equal(o, w)
+
+
+def test_fanin_out_of_range_is_rejected():
+    ids = np.arange(8, dtype=np.uint32)
+    for bad in (1, 9, -1):
+        with pytest.raises(vp.VelopirError):
+            vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, 8, bits(3, 32), id_bits=32, payload=ids, payload_bits=32,
+                                  agg_fanin=bad)
