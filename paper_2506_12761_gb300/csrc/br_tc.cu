@@ -30,7 +30,7 @@
 //     X^abar ACC - ACC -> six digit rows, reversed, as fp16 in the K-major
 //     core-matrix layout of the MMA's B operand;
 //   tc_mma_kernel: CTA = (128 output coefficients, 128 bootstraps).  Warp 0
-//     streams key windows and digit blocks into a two-stage ring with bulk
+//     streams key windows and digit blocks into a five-stage ring with bulk
 //     asynchronous copies; warp 1 issues the MMAs (M = 128 coefficients,
 //     N = 128 bootstraps, K = 16) into four limb accumulators (512 Tensor
 //     Memory columns); warps 2-5 read each row's accumulators, combine the
@@ -59,7 +59,7 @@ constexpr int KBLOCKS = kN / KB;                   // 16 stages per digit row
 constexpr int AWIN = (TM + KB) / 8;                // 24 Hankel groups per (limb, stage)
 constexpr int ABYTES = AWIN * 128;                 // 3 KB
 constexpr int BBYTES = TN * KB * 2;                // 16 KB: 128 bootstraps x 64 digits
-constexpr int kStages = 2;
+constexpr int kStages = 5;                         // ring depth: hides the L2 latency of a 28 KB stage behind 4 stages of MMAs
 constexpr uint32_t kTmemCols = 512;                // 4 limbs x 128 bootstraps
 
 // Digits in global memory: [tile of 128 bootstraps][row][k' group (128)][n group (16)][8 n][8 k'] fp16, so
@@ -67,9 +67,12 @@ constexpr uint32_t kTmemCols = 512;                // 4 limbs x 128 bootstraps
 // exactly as the B operand wants it in shared memory.
 constexpr size_t kDigTileHalves = (size_t)kRows * kN * TN;
 
+struct __align__(1024) MmaSmem;
+static_assert(kStages * (BBYTES + kLimbs * ABYTES) + TN * TM * 4 + 1024 <= 232448, "shared memory per CTA");
+
 struct __align__(1024) MmaSmem {
-    __half b[kStages][TN * KB];                    // 32 KB; placed first so that any descriptor read of it stays inside the block
-    __half a[kStages][kLimbs][AWIN * 64];          // 24 KB
+    __half b[kStages][TN * KB];                    // 80 KB; placed first so that any descriptor read of it stays inside the block
+    __half a[kStages][kLimbs][AWIN * 64];          // 60 KB
     uint32_t part[TN * TM];                        // 64 KB: integer sums, [bootstrap][coefficient]
     unsigned long long full[kStages], empty[kStages], acc_full, acc_empty;
     uint32_t tmem_base;
