@@ -392,10 +392,18 @@ __global__ void __launch_bounds__(192, 1) tc_mma_kernel(int step, int njobs, con
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&S.acc_empty);
         }
-        // ACC_j[m0 + m] += the step's product, for each bootstrap of the tile
-        for (int n = 0; n < nact; ++n) {
-            uint32_t *a = acc + ((size_t)(tile * TN + n)) * kTwoN + (size_t)j * kN + m0 + m;
-            *a += S.part[n * TM + m];
+        // ACC_j[m0 + m] += the step's product, for each bootstrap of the tile:
+        // 16 loads in flight at a time instead of one read-modify-write per
+        // L2 round trip
+        uint32_t *col = acc + ((size_t)tile * TN) * kTwoN + (size_t)j * kN + m0 + m;
+        for (int n0 = 0; n0 < nact; n0 += 16) {
+            uint32_t v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (n0 + k < nact) v[k] = __ldcg(col + (size_t)(n0 + k) * kTwoN);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (n0 + k < nact) __stcg(col + (size_t)(n0 + k) * kTwoN, v[k] + S.part[(n0 + k) * TM + m]);
         }
     }
 
