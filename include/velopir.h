@@ -392,8 +392,10 @@ int velopir_queue_depth(velopir_ctx *ctx, size_t *admitted, size_t *waiting);
 /* Wait for all work on the context's stream.  Errors: ERR_CUDA, ERR_TIMEOUT. */
 int velopir_sync(velopir_ctx *ctx);
 
-/* Message of the last failure on this context ("" if none).  NULL ctx gives
- * the last failure of velopir_create on this thread. */
+/* Message of the last failure on this context ("" if none), as a copy owned
+ * by the calling thread that stays valid until that thread's next call of
+ * this function (the issue thread may record a failure meanwhile).  NULL ctx
+ * gives the last failure of velopir_create on this thread. */
 const char *velopir_last_error(velopir_ctx *ctx);
 
 /* Kernel launches this context has issued since creation (for launch counting). */

@@ -45,6 +45,7 @@ struct velopir_ctx {
     bool own_stream = false;
     size_t budget = 0;      // 0 = unlimited
     size_t allocated = 0;   // bytes currently held
+    std::mutex err_mu;      // guards err: the issue thread and the caller may both fail
     std::string err;
     uint64_t launches = 0;
     int path = VP_PATH_NTT;
@@ -107,9 +108,19 @@ int fail(velopir_ctx *c, int code, const char *fmt, ...)
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (c) c->err = buf;
-    else g_create_error = buf;
+    if (c) {
+        std::lock_guard<std::mutex> g(c->err_mu);
+        c->err = buf;
+    } else {
+        g_create_error = buf;
+    }
     return code;
+}
+
+std::string last_error_of(velopir_ctx *c)
+{
+    std::lock_guard<std::mutex> g(c->err_mu);
+    return c->err;
 }
 
 #define CU(call)                                                                                   \
@@ -847,13 +858,13 @@ void issue_loop(velopir_ctx *c)
     while (!c->stop_req) {
         while (!c->inflight.empty() && cudaEventQuery(c->inflight.front().ev) == cudaSuccess) retire_front();
         int rc = reap(c, false);
-        if (rc && c->issuer_rc == VELOPIR_OK) { c->issuer_rc = rc; c->issuer_err = c->err; }
+        if (rc && c->issuer_rc == VELOPIR_OK) { c->issuer_rc = rc; c->issuer_err = last_error_of(c); }
         if ((!c->waiting.empty() || issuable(c)) && (int)c->inflight.size() < kMaxInflightSteps &&
             c->issuer_rc == VELOPIR_OK) {
             rc = serve_step(c);
             if (rc != VELOPIR_OK) {
                 c->issuer_rc = rc;
-                c->issuer_err = c->err;
+                c->issuer_err = last_error_of(c);
                 continue;
             }
             // a slot of the pinned error copies that no in-flight step uses
@@ -963,7 +974,7 @@ int velopir_create(velopir_ctx **out, int device, size_t hbm_budget_bytes, void 
     if (configure_br_dense() != 0 || configure_br_ntt() != 0 || configure_br_tc() != 0 || configure_key_switch() != 0)
         return fail(nullptr, VELOPIR_ERR_CUDA, "cannot raise the shared-memory limit of the blind-rotation kernels");
     int rc = ensure(c, c->errw, 256);
-    if (rc) { g_create_error = c->err; return rc; }
+    if (rc) { g_create_error = last_error_of(c); return rc; }
     CU(cudaMemsetAsync(c->errw.p, 0, 256, c->stream));
     *out = ctx.release();
     return VELOPIR_OK;
@@ -1545,7 +1556,13 @@ int velopir_sync(velopir_ctx *c)
     return check_device_error(c);
 }
 
-const char *velopir_last_error(velopir_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+const char *velopir_last_error(velopir_ctx *c)
+{
+    if (!c) return g_create_error.c_str();
+    thread_local std::string copy;   // stable for the caller while another thread may fail
+    copy = last_error_of(c);
+    return copy.c_str();
+}
 
 uint64_t velopir_launch_count(velopir_ctx *c) { return c ? c->launches : 0; }
 
