@@ -167,54 +167,71 @@ PAPER4 = [  # dataset, mode, M, l_S, the paper's "All" time (s), Table 4
 ]
 
 
-def run_paper4(ctx, s):
+def paper4_case(s, k: int) -> dict:
+    """The inputs of Table 4 shape k (PAPER4): an encrypted database of M
+    entries with l_I = 16-bit values, an encrypted l_S-bit payload per entry
+    (Alg. PubKeyGen + ServerEnc), the encrypted query, and the plaintext
+    answer (the XOR of the payloads of the valid entries)."""
     l = 16
+    name, mode, M, lS, paper_s = PAPER4[k]
+    st = synth.Stream(synth.MASTER_SEED, synth.STREAM_DB, 60 + k)
+    pay = (st.words(M) & np.uint32((1 << min(lS, 32)) - 1)).astype(np.uint64)
+    pay_bits = synth.value_bits(pay, 32)[:, :lS] if lS <= 32 else st.bits(M * lS).reshape(M, lS).astype(np.uint32)
+    P = vp.velopir_server_encrypt(
+        vp.velopir_client_pubkeygen(s, synth.lwe_material(M * lS, seed=70 + k, stream=synth.STREAM_PUBKEY)),
+        pay_bits.reshape(-1)).reshape(M, lS, 631)
+    c = dict(name=name, mode=mode, M=M, lS=lS, l=l, paper_s=paper_s, P=P)
+    if mode == "IntV":
+        x, y, rects, valid = intv_case(M, l, 80 + k)
+        c.update(cx=vp.velopir_client_encrypt_bits(s, synth.value_bits([x], l)[0], synth.lwe_material(l, substream=90 + k)),
+                 cy=vp.velopir_client_encrypt_bits(s, synth.value_bits([y], l)[0], synth.lwe_material(l, substream=100 + k)),
+                 enc=server_enc(s, rects.reshape(-1), l, 110 + k), valid=valid, boots=(12 * l + 3) * M)
+    elif mode == "CoV":
+        cells = st.words(M)
+        valid = np.zeros(M, dtype=np.uint32)
+        valid[M // 2] = 1
+        q = int(cells[M // 2])
+        c.update(cq=vp.velopir_client_encrypt_bits(s, synth.value_bits([q], 2 * l)[0],
+                                                   synth.lwe_material(2 * l, substream=90 + k)),
+                 enc=server_enc(s, cells, 2 * l, 110 + k), valid=valid, boots=(4 * l - 1) * M)
+    else:
+        ids = synth.distinct_u32(st, M, l).astype(np.uint32)
+        valid = np.zeros(M, dtype=np.uint32)
+        valid[M // 3] = 1
+        c.update(xq=vp.velopir_client_encrypt_bits(s, synth.value_bits([int(ids[M // 3])], l)[0],
+                                                   synth.lwe_material(l, substream=90 + k)),
+                 enc=server_enc(s, ids, l, 110 + k), valid=valid, boots=(2 * l - 1) * M)
+    c["boots"] += M * lS + (M - 1) * lS   # HomBitwiseAND + HomSum
+    want = np.zeros(lS, dtype=np.uint32)
+    for d in np.flatnonzero(c["valid"]):
+        want ^= pay_bits[d].astype(np.uint32)
+    c["want"] = want
+    return c
+
+
+def paper4_run(ctx, c, out) -> None:
+    """Run the full protocol of a paper4_case through the C ABI into out [l_S][631]."""
+    if c["mode"] == "IntV":
+        vp.velopir_interval_query_encdb(ctx, c["cx"], c["cy"], c["l"], c["enc"], c["M"], c["P"], c["lS"], out)
+    elif c["mode"] == "CoV":
+        vp.velopir_coordinate_query_encdb(ctx, c["cq"], c["l"], c["enc"], c["M"], c["P"], c["lS"], out)
+    else:
+        vp.velopir_id_match_encdb(ctx, c["xq"], c["l"], c["enc"], c["M"], c["P"], c["lS"], out)
+
+
+def run_paper4(ctx, s):
     res = []
-    for k, (name, mode, M, lS, paper_s) in enumerate(PAPER4):
-        st = synth.Stream(synth.MASTER_SEED, synth.STREAM_DB, 60 + k)
-        pay = (st.words(M) & np.uint32((1 << min(lS, 32)) - 1)).astype(np.uint64)
-        pay_bits = synth.value_bits(pay, 32)[:, :lS] if lS <= 32 else \
-            st.bits(M * lS).reshape(M, lS).astype(np.uint32)
-        P = vp.velopir_server_encrypt(
-            vp.velopir_client_pubkeygen(s, synth.lwe_material(M * lS, seed=70 + k, stream=synth.STREAM_PUBKEY)),
-            pay_bits.reshape(-1)).reshape(M, lS, 631)
-        out = np.zeros((lS, 631), dtype=np.uint32)
-        if mode == "IntV":
-            x, y, rects, valid = intv_case(M, l, 80 + k)
-            cx = vp.velopir_client_encrypt_bits(s, synth.value_bits([x], l)[0], synth.lwe_material(l, substream=90 + k))
-            cy = vp.velopir_client_encrypt_bits(s, synth.value_bits([y], l)[0], synth.lwe_material(l, substream=100 + k))
-            enc = server_enc(s, rects.reshape(-1), l, 110 + k)
-            call = lambda: vp.velopir_interval_query_encdb(ctx, cx, cy, l, enc, M, P, lS, out)
-            boots = (12 * l + 3) * M
-        elif mode == "CoV":
-            cells = st.words(M)
-            valid = np.zeros(M, dtype=np.uint32)
-            valid[M // 2] = 1
-            q = int(cells[M // 2])
-            cq = vp.velopir_client_encrypt_bits(s, synth.value_bits([q], 2 * l)[0], synth.lwe_material(2 * l, substream=90 + k))
-            enc = server_enc(s, cells, 2 * l, 110 + k)
-            call = lambda: vp.velopir_coordinate_query_encdb(ctx, cq, l, enc, M, P, lS, out)
-            boots = (4 * l - 1) * M
-        else:
-            ids = synth.distinct_u32(st, M, l).astype(np.uint32)
-            valid = np.zeros(M, dtype=np.uint32)
-            valid[M // 3] = 1
-            xq = vp.velopir_client_encrypt_bits(s, synth.value_bits([int(ids[M // 3])], l)[0],
-                                                synth.lwe_material(l, substream=90 + k))
-            enc = server_enc(s, ids, l, 110 + k)
-            call = lambda: vp.velopir_id_match_encdb(ctx, xq, l, enc, M, P, lS, out)
-            boots = (2 * l - 1) * M
-        boots += M * lS + (M - 1) * lS   # HomBitwiseAND + HomSum
+    for k in range(len(PAPER4)):
+        c = paper4_case(s, k)
+        out = np.zeros((c["lS"], 631), dtype=np.uint32)
         t0 = time.perf_counter()
-        call()
+        paper4_run(ctx, c, out)
         dt = time.perf_counter() - t0
-        want = np.zeros(lS, dtype=np.uint32)
-        for d in np.flatnonzero(valid):
-            want ^= pay_bits[d].astype(np.uint32)
-        ok = np.array_equal(vp.velopir_client_decrypt_bits(s, out), want)
-        res.append({"workload": f"paper4 {name} {mode} (encrypted database, M={M}, l_I={l}, l_S={lS})",
-                    "bootstraps": boots, "seconds": dt, "bootstraps_per_s": boots / dt,
-                    "paper_all_seconds": paper_s, "correct": bool(ok)})
+        ok = np.array_equal(vp.velopir_client_decrypt_bits(s, out), c["want"])
+        res.append({"workload": f"paper4 {c['name']} {c['mode']} (encrypted database, M={c['M']}, "
+                                f"l_I={c['l']}, l_S={c['lS']})",
+                    "bootstraps": c["boots"], "seconds": dt, "bootstraps_per_s": c["boots"] / dt,
+                    "paper_all_seconds": c["paper_s"], "correct": bool(ok)})
     return res
 
 

@@ -60,6 +60,12 @@ __constant__ uint2 cWp[2][2][kN];
 // (inverse) the transpose, as (w, w') pairs in [stage][group][lane] order so
 // that a warp reads them from shared memory without bank conflicts.
 __device__ uint2 gWL[2][2][kTwLane];
+// The first two forward stages of a digit polynomial by lookups.  Stage 0
+// multiplies digits d = b - 64 (b the packed byte) by its one twiddle
+// psi^512; stage 1 multiplies d + psi^512 d' by psi^256 or psi^768, which by
+// linearity (and psi^1024 = -1) is a sum of two lookups.  gTab[prime][0][b] =
+// psi^512 d, [1][b] = psi^256 d, [2][b] = psi^768 d, all mod p.
+__device__ uint32_t gTab[2][3][128];
 
 struct PrimeConsts {
     uint32_t p[2];
@@ -72,6 +78,7 @@ __constant__ PrimeConsts cP;
 template <int WARPS> struct __align__(128) Smem {
     uint32_t ring[kRing][kChunkWords];    // 2 x 16 KB: stream of the transformed key
     uint2 twl[2][2][kTwLane];             // 31 KB: lane-dependent twiddles [prime][direction]
+    uint32_t tab[2][3][128];              // 3 KB: first-two-stage products of the digits, per prime
     uint32_t acc[WARPS][2 * kN];          // 8 KB per warp: ACC of its bootstrap
     uint32_t xch[WARPS][kXch];            // 4.1 KB per warp: transpose tile
     uint16_t abar[WARPS][kSlotWords];     // modulus-switched input
@@ -274,12 +281,14 @@ __device__ __forceinline__ void transpose32(uint32_t (&x)[32], uint32_t *m, int 
 // (values below 2p), row layout out (transform order), values below 22p.  Every loop has a
 // compile-time trip count and every array index is a compile-time constant,
 // so the 32 points stay in registers.
+// S0 = 2: stages 0 and 1 were already applied (the digit path's lookups).
+template <int S0>
 __device__ __forceinline__ void ntt_fwd(uint32_t (&x)[32], int pi, uint32_t *xch, int lane, const uint2 *twl)
 {
     const uint32_t p = kP[0] + (uint32_t)pi * (kP[1] - kP[0]);
     const uint2 *cw = &cWp[pi][0][0];
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {            // distance 512 >> s: within a lane
+    for (int s = S0; s < 5; ++s) {           // distance 512 >> s: within a lane
         const int dt = 16 >> s;
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
@@ -381,6 +390,7 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
         const uint2 *src = &gWL[0][0][0];
         uint2 *dst = &S.twl[0][0][0];
         for (int k = tid; k < 4 * kTwLane; k += WARPS * 32) dst[k] = src[k];
+        for (int k = tid; k < 2 * 3 * 128; k += WARPS * 32) (&S.tab[0][0][0])[k] = (&gTab[0][0][0])[k];
     }
     if (tid == 0) {
         for (int r = 0; r < kRing; ++r) {
@@ -483,11 +493,31 @@ br_ntt_kernel(const BrJob *__restrict__ jobs, int njobs, int per, const uint32_t
 #pragma unroll 1
             for (int r = 0; r < kRows; ++r) {
                 uint32_t x[32];
+                // stages 0 and 1 by lookups.  For u < 8, with bytes b_j of
+                // digits j = u, u+8, u+16, u+24: stage 0 gives s = x_u +
+                // psi^512 d_{u+16} and s' = x_u - psi^512 d_{u+16}; stage 1
+                // pairs (u, u+8) with psi^256 and (u+16, u+24) with psi^768,
+                // whose products are psi^256 d_{u+8} + psi^768 d_{u+24} and
+                // psi^768 d_{u+8} + psi^256 d_{u+24}.  Outputs below 6p, as
+                // two multiplying stages give.
+                const uint32_t *T0 = S.tab[pi][0], *Ua = S.tab[pi][1], *Ub = S.tab[pi][2];
 #pragma unroll
-                for (int t = 0; t < 32; ++t) x[t] = __byte_perm(dw[t >> 2], 0u, 0x4440u | (t & 3)) + (p - 64u);   // digit mod p
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t b0 = __byte_perm(dw[u >> 2], 0u, 0x4440u | (u & 3));
+                    const uint32_t b8 = __byte_perm(dw[(u + 8) >> 2], 0u, 0x4440u | (u & 3));
+                    const uint32_t b16 = __byte_perm(dw[(u + 16) >> 2], 0u, 0x4440u | (u & 3));
+                    const uint32_t b24 = __byte_perm(dw[(u + 24) >> 2], 0u, 0x4440u | (u & 3));
+                    const uint32_t xv = b0 + (p - 64u), t0 = T0[b16];
+                    const uint32_t s0 = xv + t0, s1 = xv - t0 + 2 * p;
+                    const uint32_t m0 = Ua[b8] + Ub[b24], m1 = Ub[b8] + Ua[b24];
+                    x[u] = s0 + m0;
+                    x[u + 8] = s0 - m0 + 2 * p;
+                    x[u + 16] = s1 + m1;
+                    x[u + 24] = s1 - m1 + 2 * p;
+                }
                 // the next row's digits arrive while this row is transformed
                 if (r + 1 < kRows) tmem_ld8_async(tdig + 8 * (r + 1), dw);
-                ntt_fwd(x, pi, xch, lane, S.twl[pi][0]);
+                ntt_fwd<2>(x, pi, xch, lane, S.twl[pi][0]);
                 const int c = (i * 2 + pi) * kRows + r;               // chunk of the key stream
                 const int slot = c % kRing;
                 mbar_wait(&S.full[slot], (uint32_t)((c / kRing) & 1), err);
@@ -588,7 +618,7 @@ __global__ void __launch_bounds__(128) bk_ntt_kernel(const uint32_t *__restrict_
     uint32_t x[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) x[t] = src[lane + 32 * t] % p;
-    ntt_fwd(x, pi, xch[warp], lane, gWL[pi][0]);
+    ntt_fwd<0>(x, pi, xch[warp], lane, gWL[pi][0]);
     // chunk layout: [t][lane][w0, w0', w1, w1'] for transform point 32*lane + t
     uint32_t *dst = out + (id / 2) * kChunkWords + (size_t)j * 2;
 #pragma unroll
@@ -662,6 +692,15 @@ int upload_tables()
                 }
         }
     if (cudaMemcpyToSymbol(gWL, WL, sizeof WL) != cudaSuccess) return -1;
+    // psi^512, psi^256, psi^768 are the forward twiddles of stage 0 (k = 1)
+    // and stage 1 (k = 2, 3): psi^brv10(k)
+    static uint32_t Tab[2][3][128];
+    for (int pi = 0; pi < 2; ++pi)
+        for (int w = 0; w < 3; ++w)
+            for (int b = 0; b < 128; ++b)
+                Tab[pi][w][b] = (uint32_t)(((uint64_t)W[pi][0][w + 1] * (uint64_t)((b - 64 + (int64_t)kP[pi]) % kP[pi])) %
+                                           kP[pi]);
+    if (cudaMemcpyToSymbol(gTab, Tab, sizeof Tab) != cudaSuccess) return -1;
     if (cudaMemcpyToSymbol(cP, &pc, sizeof pc) != cudaSuccess) return -1;
     if (dev >= 0 && dev < 64) g_tables_ready[dev] = true;
     return 0;

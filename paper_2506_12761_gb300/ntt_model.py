@@ -5,7 +5,11 @@ Per blind-rotation step (N = 1024, two primes, l = 3 levels x 2 components):
   * 12 forward NTTs (6 digit polynomials x 2 primes) and 4 inverse NTTs
     (2 output polynomials x 2 primes), N/2 * log2(N) = 5,120 butterflies each,
     one Shoup multiplication per butterfly: a high-half product
-    floor(x w' / 2^32) and two low-half products (x w, q p);
+    floor(x w' / 2^32) and two low-half products (x w, q p) -- except the
+    first two stages of each forward NTT, whose multiplicands are 7-bit digits
+    (stage 0) or d + psi^512 d' (stage 1): their products are table lookups
+    (psi^512 d, psi^256 d, psi^768 d), no multiplication, so a forward NTT
+    executes 8 multiplying stages of 512 butterflies;
   * 2 primes x 6 rows x 2 outputs x N pointwise Shoup products against the
     stored key and its companions;
   * 2 x N Chinese-remainder lifts: one Shoup product and one low product
@@ -27,17 +31,19 @@ N = 1024
 LOG2N = 10
 STEPS = 630
 BUTTERFLIES_PER_NTT = N // 2 * LOG2N
-NTTS_PER_STEP = 12 + 4
+LOOKUP_STAGES = 2                                  # forward stages done by table lookups
+FWD_NTTS_PER_STEP, INV_NTTS_PER_STEP = 12, 4
 POINTWISE_PER_STEP = 2 * 6 * 2 * N
 CRT_PER_STEP = 2 * N
 
-SHOUP_PER_STEP = NTTS_PER_STEP * BUTTERFLIES_PER_NTT + POINTWISE_PER_STEP + CRT_PER_STEP
+SHOUP_PER_STEP = (FWD_NTTS_PER_STEP * (BUTTERFLIES_PER_NTT - LOOKUP_STAGES * N // 2)
+                  + INV_NTTS_PER_STEP * BUTTERFLIES_PER_NTT + POINTWISE_PER_STEP + CRT_PER_STEP)
 HI_PER_STEP = SHOUP_PER_STEP                       # one high-half product per Shoup multiplication
 LO_PER_STEP = 2 * SHOUP_PER_STEP + CRT_PER_STEP    # two low products per Shoup, plus p0 t in the lift
 
 IMAD_OPS_PER_STEP = HI_PER_STEP + LO_PER_STEP
-IMAD_OPS_PER_BOOTSTRAP = IMAD_OPS_PER_STEP * STEPS             # 206,438,400 multiplies
+IMAD_OPS_PER_BOOTSTRAP = IMAD_OPS_PER_STEP * STEPS             # 183,214,080 multiplies
 HI_SLOTS = 2                                                   # pipe slots of one high-half multiply
 IMAD_SLOTS_PER_STEP = HI_SLOTS * HI_PER_STEP + LO_PER_STEP
-IMAD_SLOTS_PER_BOOTSTRAP = IMAD_SLOTS_PER_STEP * STEPS         # 274,821,120 lane-slots
+IMAD_SLOTS_PER_BOOTSTRAP = IMAD_SLOTS_PER_STEP * STEPS         # 243,855,360 lane-slots
 DENSE_MACS_PER_BOOTSTRAP = 12 * N * N * STEPS                  # 7,927,234,560
