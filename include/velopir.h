@@ -104,6 +104,15 @@ int velopir_set_path(velopir_ctx *ctx, velopir_path path);
  * under every cap.  Errors: ERR_ARG. */
 int velopir_set_launch_limit(velopir_ctx *ctx, size_t max_rotations);
 
+/* Fan-in of the XOR aggregation tree of the *_encdb calls with a payload
+ * (default 2; 0 restores it).  2 is Section 5's pairwise HomSum, (D-1) l_S
+ * bootstraps; g in 3..8 XORs g values with one bootstrap
+ * of 2 sum c_k + T((g-1)/4), ceil((D-1)/(g-1)) l_S bootstraps at most, in
+ * ceil(log_g D) levels.  The plaintext answer is the same for every g; the
+ * noise margin falls with g (about 18 sigma at 2, 9 sigma at 8).
+ * Errors: ERR_ARG, ERR_BUSY. */
+int velopir_set_encdb_fanin(velopir_ctx *ctx, int fanin);
+
 /* One gate on each of `count` independent inputs, all bootstraps issued as
  * one batch (blind rotation of every input shares each step's BK_i).
  *   lwe_in : uint32_t[count][arity][631], arity 2 (3 for VP_MUX: c, a, b)
@@ -211,7 +220,8 @@ int velopir_id_match(velopir_ctx *ctx, const uint32_t *enc_id, int id_bits, cons
  * [D][payload_bits][631] (1 <= payload_bits <= VELOPIR_MAX_ENC_PAYLOAD_BITS,
  * the paper's l_S), each entry's payload is zeroed by its validation bit with
  * one bootstrapped AND per bit (Alg. HomBitwiseAND) and the D results are
- * XOR-aggregated pairwise (Section 5's HomSum, (D-1) payload_bits bootstraps):
+ * XOR-aggregated by a tree of the context's fan-in (velopir_set_encdb_fanin;
+ * by default pairwise, Section 5's HomSum, (D-1) payload_bits bootstraps):
  * out = [payload_bits][631], the XOR of the payloads of the valid entries. */
 
 /* IntV over an encrypted database (Alg. InterValid): validation bit
@@ -252,7 +262,9 @@ typedef struct {
                                 parity of the true inputs (about (D - 1)/(g - 1) bootstraps per
                                 bit).  The doubled input noise against the 1/4 margin stays
                                 above 9 standard deviations of tfhe-2's output-noise bound up to
-                                g = 8.  Same plaintext result, different ciphertexts. */
+                                g = 8.  Same plaintext result, different ciphertexts.
+                                velopir_plan_query also takes it for the VP_PLAN_*_ENCDB kinds
+                                (the fan-in velopir_set_encdb_fanin sets). */
     const uint32_t *enc_a;   /* IntV: enc_x; CoV: enc_cell; IdM: enc_id (host or device) */
     const uint32_t *enc_b;   /* IntV: enc_y; otherwise NULL */
     const uint32_t *db;      /* rects / cells / ids (host or device; copied at submit) */

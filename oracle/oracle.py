@@ -500,16 +500,19 @@ def idm_enc_batch(keys: Keys, x_cts, enc_ids, threads: int | None = None) -> np.
     return np.stack(out) if out else np.zeros((0, keys.P.n + 1), np.uint32)
 
 
-def aggregate_enc(keys: Keys, v, enc_payload, threads: int | None = None) -> np.ndarray:
+def aggregate_enc(keys: Keys, v, enc_payload, threads: int | None = None, fanin: int = 2) -> np.ndarray:
     """Alg. HomBitwiseAND with encrypted payloads (one bootstrapped AND of each
     entry's validation bit v[d] with each of its payload bits), then the
-    HomSum XOR tree.  enc_payload: [D][lS][n+1]; returns [lS][n+1]."""
+    HomSum XOR tree (fanin 2) or the fan-in-g tree of homsum_tree_fanin.
+    enc_payload: [D][lS][n+1]; returns [lS][n+1]."""
     v = _u32(v)
     Pay = _u32(enc_payload)
     D, lS = Pay.shape[0], Pay.shape[1]
     with _pool(threads) as ex:
         flat = list(ex.map(lambda k: gate(keys, AND, v[k // lS], Pay[k // lS, k % lS]), range(D * lS)))
     S = np.stack(flat).reshape(D, lS, -1)
+    if fanin > 2:
+        return homsum_tree_fanin(keys, S, fanin, threads)
     return homsum_tree(keys, S, threads)
 
 

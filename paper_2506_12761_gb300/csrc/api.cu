@@ -50,6 +50,7 @@ struct velopir_ctx {
     uint64_t launches = 0;
     int path = VP_PATH_NTT;
     int big_rows = 1 << 16; // blind rotations per launch at most (extracted-row scratch)
+    int enc_fanin = 2;      // fan-in of the *_encdb calls' XOR aggregation tree
 
     bool key_loaded = false;
     DevBuf bk, ksk, bk_ntt, big, jobs_br, jobs_ks, jobs_fr, jobs_sm, jobs_tr, pool, in, out, errw;
@@ -1049,6 +1050,16 @@ int velopir_set_launch_limit(velopir_ctx *c, size_t max_rotations)
     return VELOPIR_OK;
 }
 
+int velopir_set_encdb_fanin(velopir_ctx *c, int fanin)
+{
+    if (!c) return fail(c, VELOPIR_ERR_ARG, "ctx is NULL");
+    if (int rc = busy(c)) return rc;
+    if (fanin != 0 && (fanin < 2 || fanin > kMaxFanin))
+        return fail(c, VELOPIR_ERR_ARG, "fanin must be 0 or in [2, %d]", kMaxFanin);
+    c->enc_fanin = fanin ? fanin : 2;
+    return VELOPIR_OK;
+}
+
 static int bootstrap_common(velopir_ctx *c, velopir_gate gate, const uint32_t *lwe_in, uint32_t *lwe_out,
                             size_t count, bool plain)
 {
@@ -1310,7 +1321,7 @@ int velopir_interval_query_encdb(velopir_ctx *c, const uint32_t *enc_x, const ui
                      D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
                      [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
                          const std::vector<Ref> x = inputs_of(B, dev[0], l), y = inputs_of(B, dev[1], l);
-                         build_intv_enc(B, x.data(), y.data(), l, dev[2], D, dev[3], pb, o);
+                         build_intv_enc(B, x.data(), y.data(), l, dev[2], D, dev[3], pb, o, c->enc_fanin);
                      });
 }
 
@@ -1328,7 +1339,7 @@ int velopir_coordinate_query_encdb(velopir_ctx *c, const uint32_t *enc_cell, int
                      D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
                      [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
                          const std::vector<Ref> cell = inputs_of(B, dev[0], 2 * w);
-                         build_cov_enc(B, cell.data(), w, dev[2], D, dev[3], pb, o);
+                         build_cov_enc(B, cell.data(), w, dev[2], D, dev[3], pb, o, c->enc_fanin);
                      });
 }
 
@@ -1346,7 +1357,7 @@ int velopir_id_match_encdb(velopir_ctx *c, const uint32_t *enc_id, int id_bits, 
                      D * (size_t)pb, out, enc_payload ? (size_t)pb : D,
                      [&](Builder &B, const uint32_t *const *dev, uint32_t *o) {
                          const std::vector<Ref> id = inputs_of(B, dev[0], id_bits);
-                         build_idm_enc(B, id.data(), id_bits, dev[2], D, dev[3], pb, o);
+                         build_idm_enc(B, id.data(), id_bits, dev[2], D, dev[3], pb, o, c->enc_fanin);
                      });
 }
 

@@ -183,8 +183,9 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
     if (kind == VP_PLAN_COV_ENCDB && (width < 1 || width > 16)) return VELOPIR_ERR_ARG;
     if (q->payload && (q->payload_bits < 1 || q->payload_bits > 32)) return VELOPIR_ERR_ARG;
     if (q->payload && (kind == VP_QUERY_INTV || kind == VP_QUERY_COV)) return VELOPIR_ERR_ARG;   // no payload form
-    if (q->agg_fanin != 0 && (q->agg_fanin < 2 || q->agg_fanin > kMaxFanin || kind != VP_QUERY_IDM))
+    if (q->agg_fanin != 0 && (q->agg_fanin < 2 || q->agg_fanin > kMaxFanin || (kind != VP_QUERY_IDM && !encdb)))
         return VELOPIR_ERR_ARG;
+    const int fanin = q->agg_fanin >= 2 ? q->agg_fanin : 2;
     if (launch_sizes && max_launches < 0) return VELOPIR_ERR_ARG;
 
     // stand-in device addresses: distinct, 16-byte aligned, never dereferenced
@@ -208,14 +209,13 @@ extern "C" int velopir_plan_query(const velopir_query *q, int wave, const uint32
     case VP_QUERY_INTV: build_intv(B, a.data(), b.data(), q->db, q->D, out); break;
     case VP_QUERY_COV: build_cov(B, a.data(), q->db, q->D, out); break;
     case VP_QUERY_IDM:
-        build_idm(B, a.data(), width, q->db, q->D, q->payload, q->payload_bits, out,
-                  q->agg_fanin >= 2 ? q->agg_fanin : 2);
+        build_idm(B, a.data(), width, q->db, q->D, q->payload, q->payload_bits, out, fanin);
         break;
     case VP_PLAN_INTV_ENCDB:
-        build_intv_enc(B, a.data(), b.data(), width, edb, q->D, pb ? epay : nullptr, pb, out);
+        build_intv_enc(B, a.data(), b.data(), width, edb, q->D, pb ? epay : nullptr, pb, out, fanin);
         break;
-    case VP_PLAN_COV_ENCDB: build_cov_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out); break;
-    default: build_idm_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out); break;
+    case VP_PLAN_COV_ENCDB: build_cov_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out, fanin); break;
+    default: build_idm_enc(B, a.data(), width, edb, q->D, pb ? epay : nullptr, pb, out, fanin); break;
     }
     relayer(P, wave);
     allocate_slots(P);

@@ -242,6 +242,40 @@ void build_cov(Builder &B, const Ref *cell, const uint32_t *cells, size_t D, uin
     }
 }
 
+// XOR over the D entries of S[d * bits + j], per bit j, into out[j]: Section
+// 5's pairwise HomSum tree (fanin 2), or the fan-in-g tree whose nodes XOR g
+// values with one bootstrap (Builder::xor_many).  D = 1 writes nothing.
+static void xor_tree(Builder &B, std::vector<Ref> &S, size_t D, int bits, uint32_t *out, int fanin)
+{
+    if (fanin > 2) {
+        // for k = 1, g, g^2, ... the members i, i + k, ..., i + (g-1)k (those
+        // below D) of each group are XORed into member i; the level with
+        // g k >= D writes `out`
+        const size_t g = (size_t)std::min(fanin, kMaxFanin);
+        Ref grp[kMaxFanin];
+        for (size_t k = 1; k < D; k *= g)
+            for (size_t i = 0; i < D; i += g * k) {
+                size_t m = 0;
+                while (m < g && i + m * k < D) ++m;
+                if (m < 2) continue;
+                for (int j = 0; j < bits; ++j) {
+                    for (size_t q = 0; q < m; ++q) grp[q] = S[(i + q * k) * bits + j];
+                    uint32_t *o = (g * k >= D && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                    S[i * bits + j] = B.xor_many(grp, (int)m, o);
+                }
+            }
+        return;
+    }
+    size_t last_k = 0;
+    for (size_t k = 1; k < D; k *= 2) last_k = k;
+    for (size_t k = 1; k < D; k *= 2)
+        for (size_t i = 0; i + k < D; i += 2 * k)
+            for (int j = 0; j < bits; ++j) {
+                uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
+                S[i * bits + j] = B.gate(G_XOR, S[i * bits + j], S[(i + k) * bits + j], o);
+            }
+}
+
 void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size_t D, const uint32_t *payload,
                int payload_bits, uint32_t *out, int fanin)
 {
@@ -258,33 +292,7 @@ void build_idm(Builder &B, const Ref *id, int id_bits, const uint32_t *ids, size
     for (size_t d = 0; d < D; ++d)
         for (int j = 0; j < payload_bits; ++j)
             S[d * payload_bits + j] = ((payload[d] >> j) & 1u) ? v[d] : Builder::trivial(0u - kMu);
-    if (fanin > 2) {
-        // Fan-in-g tree: for k = 1, g, g^2, ... the members i, i + k, ...,
-        // i + (g-1)k (those below D) of each group are XORed with one
-        // bootstrap into member i; the level with g k >= D writes `out`.
-        const size_t g = (size_t)std::min(fanin, kMaxFanin);
-        Ref grp[kMaxFanin];
-        for (size_t k = 1; k < D; k *= g)
-            for (size_t i = 0; i < D; i += g * k) {
-                size_t m = 0;
-                while (m < g && i + m * k < D) ++m;
-                if (m < 2) continue;
-                for (int j = 0; j < payload_bits; ++j) {
-                    for (size_t q = 0; q < m; ++q) grp[q] = S[(i + q * k) * payload_bits + j];
-                    uint32_t *o = (g * k >= D && i == 0) ? out + (size_t)j * kLweWords : nullptr;
-                    S[i * payload_bits + j] = B.xor_many(grp, (int)m, o);
-                }
-            }
-    } else {
-        size_t last_k = 0;
-        for (size_t k = 1; k < D; k *= 2) last_k = k;
-        for (size_t k = 1; k < D; k *= 2)
-            for (size_t i = 0; i + k < D; i += 2 * k)
-                for (int j = 0; j < payload_bits; ++j) {
-                    uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
-                    S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
-                }
-    }
+    xor_tree(B, S, D, payload_bits, out, fanin);
     if (D == 1)
         for (int j = 0; j < payload_bits; ++j) B.materialize(S[j], out + (size_t)j * kLweWords);
 }
@@ -334,7 +342,7 @@ static std::vector<Ref> enc_inputs(Builder &B, const uint32_t *base, int count)
 // validation bit with each payload bit), then the pairwise HomSum XOR
 // reduction of Section 5 per payload bit into out.
 static void aggregate_enc(Builder &B, const std::vector<Ref> &v, const uint32_t *enc_payload, int payload_bits,
-                          uint32_t *out)
+                          uint32_t *out, int fanin)
 {
     const size_t D = v.size();
     std::vector<Ref> S(D * (size_t)payload_bits);
@@ -343,18 +351,11 @@ static void aggregate_enc(Builder &B, const std::vector<Ref> &v, const uint32_t 
         for (int j = 0; j < payload_bits; ++j)
             S[d * payload_bits + j] = B.gate(G_AND, v[d], pay[j], (D == 1) ? out + (size_t)j * kLweWords : nullptr);
     }
-    size_t last_k = 0;
-    for (size_t k = 1; k < D; k *= 2) last_k = k;
-    for (size_t k = 1; k < D; k *= 2)
-        for (size_t i = 0; i + k < D; i += 2 * k)
-            for (int j = 0; j < payload_bits; ++j) {
-                uint32_t *o = (k == last_k && i == 0) ? out + (size_t)j * kLweWords : nullptr;
-                S[i * payload_bits + j] = B.gate(G_XOR, S[i * payload_bits + j], S[(i + k) * payload_bits + j], o);
-            }
+    xor_tree(B, S, D, payload_bits, out, fanin);
 }
 
 void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D,
-                    const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+                    const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin)
 {
     // Alg. InterValid with encrypted bounds: AND(AND(LE(x_lo,x), L(x,x_hi)), AND(LE(y_lo,y), L(y,y_hi))).
     std::vector<Ref> v(D);
@@ -368,11 +369,11 @@ void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_
         Ref vy = B.gate(G_AND, vyl, vyr);
         v[d] = B.gate(G_AND, vx, vy, enc_payload ? nullptr : out + d * kLweWords);
     }
-    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out, fanin);
 }
 
 void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D,
-                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin)
 {
     // Alg. CoV with encrypted cells: AND(HomEqOPT(x, loc_x), HomEqOPT(y, loc_y)).
     std::vector<Ref> v(D);
@@ -382,18 +383,18 @@ void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells
         Ref vy = build_eq_enc(B, cell + w, c.data() + w, w);
         v[d] = B.gate(G_AND, vx, vy, enc_payload ? nullptr : out + d * kLweWords);
     }
-    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out, fanin);
 }
 
 void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
-                   const uint32_t *enc_payload, int payload_bits, uint32_t *out)
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin)
 {
     std::vector<Ref> v(D);
     for (size_t d = 0; d < D; ++d) {
         const std::vector<Ref> c = enc_inputs(B, enc_ids + d * (size_t)id_bits * kLweWords, id_bits);
         v[d] = build_eq_enc(B, id, c.data(), id_bits, enc_payload ? nullptr : out + d * kLweWords);
     }
-    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out);
+    if (enc_payload) aggregate_enc(B, v, enc_payload, payload_bits, out, fanin);
 }
 
 void layer_chunks(const Layer &L, int cap, std::vector<Chunk> &out)

@@ -111,15 +111,16 @@ Ref build_eq_enc(Builder &B, const Ref *x, const Ref *y, int l, uint32_t *out = 
 // enc_rects: [D][4][l] ciphertexts (x_lo, x_hi, y_lo, y_hi).  With
 // enc_payload ([D][payload_bits] ciphertexts) each entry's payload is zeroed
 // by its validation bit and the results are XOR-aggregated into out
-// ([payload_bits] ciphertexts); without it out receives the D bits.
+// ([payload_bits] ciphertexts) by a tree of fan-in `fanin` (2: Section 5's
+// pairwise HomSum); without it out receives the D bits.
 void build_intv_enc(Builder &B, const Ref *x, const Ref *y, int l, const uint32_t *enc_rects, size_t D,
-                    const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+                    const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin = 2);
 // cell: 2w ciphertexts (x then y); enc_cells: [D][2w].
 void build_cov_enc(Builder &B, const Ref *cell, int w, const uint32_t *enc_cells, size_t D,
-                   const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin = 2);
 // enc_ids: [D][id_bits].
 void build_idm_enc(Builder &B, const Ref *id, int id_bits, const uint32_t *enc_ids, size_t D,
-                   const uint32_t *enc_payload, int payload_bits, uint32_t *out);
+                   const uint32_t *enc_payload, int payload_bits, uint32_t *out, int fanin = 2);
 
 // Wave-filling list schedule (replaces the as-soon-as-possible layers of a
 // built program, before allocate_slots).  A gate may run in any launch after

@@ -42,7 +42,7 @@ EXPORTS = [
     "velopir_selftest_wait_timeout", "velopir_plan_query",
     "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb", "velopir_cancel",
     "velopir_plan_batch", "velopir_trace_start", "velopir_trace_stop", "velopir_set_launch_limit",
-    "velopir_serve_start", "velopir_serve_stop",
+    "velopir_serve_start", "velopir_serve_stop", "velopir_set_encdb_fanin",
 ]
 # Every symbol include/velopir_client.h declares (the host-only client library).
 CLIENT_EXPORTS = [
@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "velopir_load_cloud_key": (i, [vp, ctypes.POINTER(Params), vp, sz, vp, sz]),
             "velopir_set_path": (i, [vp, i]),
             "velopir_set_launch_limit": (i, [vp, sz]),
+            "velopir_set_encdb_fanin": (i, [vp, i]),
             "velopir_serve_start": (i, [vp]),
             "velopir_serve_stop": (i, [vp]),
             "velopir_bootstrap_batch": (i, [vp, i, vp, vp, sz]),
@@ -209,6 +210,11 @@ def velopir_set_path(ctx, path: int) -> None:
 def velopir_set_launch_limit(ctx, max_rotations: int) -> None:
     """Blind rotations per launch at most (1: one bootstrap per launch; 0: default)."""
     _check(ctx, lib().velopir_set_launch_limit(ctx, max_rotations))
+
+
+def velopir_set_encdb_fanin(ctx, fanin: int) -> None:
+    """Fan-in of the *_encdb calls' XOR aggregation tree (2: pairwise HomSum; 0: default)."""
+    _check(ctx, lib().velopir_set_encdb_fanin(ctx, fanin))
 
 
 def velopir_bootstrap_batch(ctx, gate: int, lwe_in, lwe_out, count: int) -> None:

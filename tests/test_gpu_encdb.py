@@ -109,3 +109,40 @@ def test_encdb_bad_arguments():
     with pytest.raises(vp.VelopirError):
         vp.velopir_id_match_encdb(ctx.h, z, 33, z, 1, None, 0, z)
     vp.velopir_id_match_encdb(ctx.h, z, 4, z, 0, None, 0, z)   # D = 0 is a no-op
+
+
+@pytest.mark.parametrize("fanin", [4, 8])
+def test_encdb_fanin_aggregation_matches_oracle(paper_keys, fanin):
+    """velopir_set_encdb_fanin: the HomBitwiseAND results of D = 11 entries
+    XOR-aggregated by the fan-in-g tree, bit-identical to the oracle's
+    composition (match bits, ANDs, homsum_tree_fanin), for IdM and CoV."""
+    ctx, s = gpu_ctx()
+    l, lS, D = 6, 5, 11
+    rng = np.random.default_rng(940 + fanin)
+    ids = rng.choice(1 << l, size=D, replace=False).astype(np.uint32)
+    pay = rng.integers(0, 1 << lS, size=D, dtype=np.uint64).astype(np.uint32)
+    xq = encrypt_value_bits(s, int(ids[4]), l, 941)
+    E = server_enc(s, ids, l, 942)
+    P = server_enc(s, pay, lS, 943)
+    vp.velopir_set_encdb_fanin(ctx.h, fanin)
+    try:
+        agg = np.zeros((lS, 631), dtype=np.uint32)
+        vp.velopir_id_match_encdb(ctx.h, xq, l, E, D, P, lS, agg)
+        w = 3
+        cells = (ids & np.uint32(0x3F)).astype(np.uint32)
+        cells[::3] = cells[1]
+        cq = encrypt_value_bits(s, int(cells[1]), 2 * w, 944)
+        C = server_enc(s, cells, 2 * w, 945)
+        cagg = np.zeros((lS, 631), dtype=np.uint32)
+        vp.velopir_coordinate_query_encdb(ctx.h, cq, w, C, D, P, lS, cagg)
+    finally:
+        vp.velopir_set_encdb_fanin(ctx.h, 0)
+    m = oracle.idm_enc_batch(paper_keys, xq, E)
+    assert np.array_equal(agg, oracle.aggregate_enc(paper_keys, m, P, fanin=fanin))
+    assert np.array_equal(vp.velopir_client_decrypt_bits(s, agg), synth.value_bits([pay[4]], lS)[0])
+    v = oracle.cov_enc_batch(paper_keys, cq, C, w)
+    assert np.array_equal(cagg, oracle.aggregate_enc(paper_keys, v, P, fanin=fanin))
+    want = np.bitwise_xor.reduce(pay[cells == cells[1]])
+    assert np.array_equal(vp.velopir_client_decrypt_bits(s, cagg), synth.value_bits([want], lS)[0])
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_set_encdb_fanin(ctx.h, 9)

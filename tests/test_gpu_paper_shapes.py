@@ -6,9 +6,9 @@ and the HomSum XOR tree.
   * gdacs CoV (M = 9, l_S = 16, 839 bootstraps): the whole circuit equals the
     oracle's from the query's own ciphertexts;
   * covid-usa IntV (M = 58, l_S = 22, 13,840 bootstraps) and weather-usa IdM
-    (M = 304, l_S = 128, 87,120 bootstraps): traced gates of every launch
-    recomputed by the oracle, and the aggregate decrypts to the XOR of the
-    valid entries' payloads."""
+    (M = 304, l_S = 128, 87,120 bootstraps; 53,968 with the fan-in-8 XOR
+    tree): traced gates of every launch recomputed by the oracle, and the
+    aggregate decrypts to the XOR of the valid entries' payloads."""
 import numpy as np
 import pytest
 
@@ -34,15 +34,21 @@ def test_gdacs_cov_whole_protocol_equals_oracle(paper_keys):
     assert np.array_equal(out, oracle.aggregate_enc(paper_keys, v, c["P"]))
 
 
-@pytest.mark.parametrize("name, mode, one_in", [("covid-usa", "IntV", 8), ("weather-usa", "IdM", 60)])
-def test_paper_shape_traced(paper_keys, name, mode, one_in):
+@pytest.mark.parametrize("name, mode, one_in, fanin", [("covid-usa", "IntV", 8, 2), ("weather-usa", "IdM", 60, 2),
+                                                       ("weather-usa", "IdM", 40, 8)])
+def test_paper_shape_traced(paper_keys, name, mode, one_in, fanin):
     ctx, s = gpu_ctx()
     c = cb.paper4_case(s, _case(name, mode))
     out = np.zeros((c["lS"], 631), dtype=np.uint32)
+    vp.velopir_set_encdb_fanin(ctx.h, fanin)
     vp.velopir_trace_start(ctx.h, 4242, 8, one_in, 4096)
-    cb.paper4_run(ctx.h, c, out)
-    recs = vp.velopir_trace_stop(ctx.h, 4096)
+    try:
+        cb.paper4_run(ctx.h, c, out)
+    finally:
+        recs = vp.velopir_trace_stop(ctx.h, 4096)
+        vp.velopir_set_encdb_fanin(ctx.h, 0)
     assert len(recs) < 4096
     assert np.array_equal(vp.velopir_client_decrypt_bits(s, out), c["want"])
     assert (recs["nrot"] == 2).any() == (mode == "IntV")   # the comparators' MUXes
+    assert (recs["nin"] == fanin).any() if fanin > 2 else (recs["nin"] <= 3).all()
     check_trace(paper_keys, recs, 800)

@@ -168,3 +168,18 @@ def test_fanin_noise_against_the_bootstrap_bound(paper_keys):
         sd = np.sqrt(4 * g * var_out + var_ms)
         assert 0.25 / sd > (9.0 if g <= 8 else 0), (g, 0.25 / sd)
     assert 0.25 / np.sqrt(4 * 16 * var_out + var_ms) < 7.0
+
+
+@pytest.mark.parametrize("g", [2, 4])
+def test_aggregate_enc_fanin_decrypts_to_the_valid_payloads(toy_keys, g):
+    """HomBitwiseAND of encrypted validation bits with encrypted payloads, then
+    the fan-in-g tree: the XOR of the payloads whose bit is 1 (g = 2 is the
+    pairwise HomSum)."""
+    n = toy_keys.P.n
+    D, lS = 6, 3
+    v_bits = np.array([1, 0, 1, 1, 0, 0], dtype=np.uint32)
+    pay = synth.Stream(80 + g, 3, 0).bits(D * lS).reshape(D, lS)
+    v = oracle.encrypt_bits(toy_keys.s, v_bits, synth.lwe_material(D, n, seed=81 + g))
+    P = oracle.encrypt_bits(toy_keys.s, pay.reshape(-1), synth.lwe_material(D * lS, n, seed=82 + g))
+    out = oracle.aggregate_enc(toy_keys, v, P.reshape(D, lS, n + 1), fanin=g)
+    assert list(oracle.decrypt_bits(toy_keys.s, out)) == list(pay[v_bits == 1].sum(axis=0) % 2)

@@ -270,3 +270,56 @@ def test_fanin_out_of_range_is_rejected():
         with pytest.raises(vp.VelopirError):
             vp.velopir_plan_query(vp.VP_QUERY_IDM, ids, 8, bits(3, 32), id_bits=32, payload=ids, payload_bits=32,
                                   agg_fanin=bad)
+
+
+@pytest.mark.parametrize("fanin", [3, 8])
+@pytest.mark.parametrize("wave", [0, 64])
+def test_encdb_fanin_tree_plans(fanin, wave):
+    """The encrypted-database calls' aggregation with the fan-in-g tree
+    (velopir_set_encdb_fanin): each of the three modes answers the XOR of
+    the valid entries' payloads and costs its validation bootstraps, one
+    AND per payload bit and entry (Alg. HomBitwiseAND), and
+    nodes(D, g) per payload bit."""
+    rng = np.random.default_rng(90 + fanin)
+    l, w, idb, pb = 8, 5, 12, 16
+    for D in (1, fanin + 1, 41):
+        pay = rng.integers(0, 1 << pb, size=D, dtype=np.uint64).astype(np.uint32)
+        agg_cost = pb * D + pb * fanin_nodes(D, fanin)
+        # IntV at l bits: entries 0 and D-1 contain the point
+        x, y = int(rng.integers(1, 255)), int(rng.integers(1, 255))
+        rects = rng.integers(0, 256, size=(D, 4), dtype=np.uint64).astype(np.uint32)
+        rects[0] = (x, x + 1, y, y + 1)
+        rects[D - 1] = (0, 255, 0, 255)
+        r = rects.astype(np.int64)
+        valid = (r[:, 0] <= x) & (x < r[:, 1]) & (r[:, 2] <= y) & (y < r[:, 3])
+        out, sizes = vp.velopir_plan_query(vp.VP_PLAN_INTV_ENCDB, rects, D, bits(x, l), bits(y, l), wave=wave,
+                                           id_bits=l, payload=pay, payload_bits=pb, agg_fanin=fanin)
+        assert np.array_equal(out, bits(np.bitwise_xor.reduce(pay[valid]), pb)), (D, fanin)
+        launches_are_waves(sizes, wave, (12 * l + 3) * D + agg_cost)
+        # CoV: a quarter of the cells equal the query's
+        cells = rng.integers(0, 1 << (2 * w), size=D, dtype=np.uint64).astype(np.uint32)
+        q = int(cells[0])
+        cells[::4] = q
+        out, sizes = vp.velopir_plan_query(vp.VP_PLAN_COV_ENCDB, cells, D, bits(q, 2 * w), wave=wave, id_bits=w,
+                                           payload=pay, payload_bits=pb, agg_fanin=fanin)
+        assert np.array_equal(out, bits(np.bitwise_xor.reduce(pay[cells == q]), pb)), (D, fanin)
+        launches_are_waves(sizes, wave, (4 * w - 1) * D + agg_cost)
+        # IdM: distinct identifiers, one match
+        ids = rng.choice(1 << idb, size=D, replace=False).astype(np.uint32)
+        hit = D // 2
+        out, sizes = vp.velopir_plan_query(vp.VP_PLAN_IDM_ENCDB, ids, D, bits(int(ids[hit]), idb), wave=wave,
+                                           id_bits=idb, payload=pay, payload_bits=pb, agg_fanin=fanin)
+        assert np.array_equal(out, bits(int(pay[hit]), pb)), (D, fanin)
+        launches_are_waves(sizes, wave, (2 * idb - 1) * D + agg_cost)
+
+
+def test_fanin_only_where_there_is_an_xor_tree():
+    """agg_fanin is accepted for IdM and the encrypted-database kinds, not
+    for the plaintext IntV and CoV calls (their outputs are per-entry bits)."""
+    rects, bx, by, _ = intv_case(4, 5)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, 4, bx, by, agg_fanin=4)
+    ids = np.arange(4, dtype=np.uint32)
+    with pytest.raises(vp.VelopirError):
+        vp.velopir_plan_query(vp.VP_PLAN_IDM_ENCDB, ids, 4, bits(1, 8), id_bits=8, payload=ids, payload_bits=8,
+                              agg_fanin=9)
