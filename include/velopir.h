@@ -463,6 +463,45 @@ typedef struct {
     uint32_t out[VELOPIR_LWE_WORDS];                     /* the gate's output */
 } velopir_trace_rec;
 
+/* ---- Client-side preprocessing on the GPU -------------------------------
+ * The computations of libvelopir_client.so (velopir_client.h) run as CUDA
+ * kernels, from the same caller-supplied random numbers, with bit-identical
+ * results: a cloud key generated here can be passed (device pointers) straight
+ * to velopir_load_cloud_key, and a server can run Alg. ServerEnc over a large
+ * database on the device that evaluates it.  Every buffer may be host or
+ * device memory; host buffers are staged through stream-ordered temporaries
+ * released before the call returns.  The context's key need not be loaded.
+ * Synchronous.  Errors: ERR_ARG (null buffer, other parameters, count above
+ * 2^24), ERR_OOM (staging), ERR_CUDA, ERR_BUSY (the issue thread runs). */
+
+/* Section 2.2 KeyGen of the cloud key: BK_i row r = 2(p-1)+q is the TRLWE
+ * sample (a, a K + e) under the TRLWE key K, plus s_i 2^(32-7p) on component q
+ * (TRGSW encryption of s_i, Bg = 2^7); KSK[i][j][v] = (a, <a, s> + v K_i
+ * 2^(32-2(j+1)) + e).  Inputs and outputs as velopir_client_keygen:
+ * s[630], K[1024] key bits (0/1), bk_a/bk_e uint32_t[630][6][1024],
+ * ksk_a uint32_t[1024][8][4][630], ksk_e uint32_t[1024][8][4]; bk_out
+ * uint32_t[630][6][2][1024], ksk_out uint32_t[1024][8][4][631]. */
+int velopir_gpu_keygen(velopir_ctx *ctx, const velopir_params *params, const uint32_t *s, const uint32_t *K,
+                       const uint32_t *bk_a, const uint32_t *bk_e, const uint32_t *ksk_a, const uint32_t *ksk_e,
+                       uint32_t *bk_out, uint32_t *ksk_out);
+
+/* Section 2.2 Enc with Ecd (1 -> 1/8, 0 -> -1/8): out_c = (a_c, <a_c, s> +
+ * Ecd(bits_c) + e_c).  s uint32_t[630] (0/1), bits uint32_t[count], a
+ * uint32_t[count][630], e uint32_t[count], out uint32_t[count][631].
+ * count == 0 is a no-op. */
+int velopir_gpu_encrypt_bits(velopir_ctx *ctx, const uint32_t *s, const uint32_t *bits, const uint32_t *a,
+                             const uint32_t *e, size_t count, uint32_t *out);
+
+/* Alg. PubKeyGen: count encryptions of zero, pk_c = (a_c, <a_c, s> + e_c);
+ * layouts as velopir_gpu_encrypt_bits. */
+int velopir_gpu_pubkeygen(velopir_ctx *ctx, const uint32_t *s, const uint32_t *a, const uint32_t *e, size_t count,
+                          uint32_t *pk_out);
+
+/* Alg. ServerEnc: ct_c = (0, Ecd(bits_c)) + pk_c.  pk and ct_out
+ * uint32_t[count][631], bits uint32_t[count] (0/1).  Uses no secret. */
+int velopir_gpu_server_encrypt(velopir_ctx *ctx, const uint32_t *pk, const uint32_t *bits, size_t count,
+                               uint32_t *ct_out);
+
 /* Start recording a sample of the gates that this context's programs and
  * serving steps execute (velopir_bootstrap_batch, the query calls,
  * velopir_query_batch with or without graph capture, velopir_submit; not

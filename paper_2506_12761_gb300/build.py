@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libvelopir.so")
 CLIENT_LIB = os.path.join(HERE, "libvelopir_client.so")
 CLIENT_SOURCE = "client.cpp"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "br_dense.cu", "br_ntt.cu", "br_tc.cu", "keyswitch.cu", "sched.cpp", "plan.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "br_dense.cu", "br_ntt.cu", "br_tc.cu", "keyswitch.cu", "sched.cpp", "plan.cpp", "noalloc.cu", "client_gpu.cu"]
 
 
 def nvcc() -> str:

@@ -20,6 +20,10 @@ checked by decrypting every output against its plaintext answer:
            (M = 9, l_S = 9), covid-usa IntV/IdM (58, 22), gdacs CoV (9, 16),
            weather-usa IdM (304, 128); printed beside the paper's "All"
            times, which were measured on its CPU + RTX 4060 Ti (context only)
+  client   the client-side preprocessing on the GPU (velopir_gpu_keygen,
+           velopir_gpu_pubkeygen; device buffers) beside the host client
+           library on the machine's cores: the cloud key (BK 31 MB, KSK 83 MB) and
+           32,768 encryptions of zero (Alg. PubKeyGen), outputs compared
 
 Inputs are synthetic and seeded (synth).  Times are wall-clock around the
 synchronous library calls (host buffers in and out, program scheduling
@@ -242,6 +246,51 @@ def run_paper4(ctx, s):
     return res
 
 
+def run_client(ctx, s):
+    """Cloud key and Alg. PubKeyGen on the GPU against the host client library."""
+    import torch
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+    km = synth.key_material()
+    t0 = time.perf_counter()
+    bk_h, ksk_h = vp.velopir_client_keygen(km)
+    t_host = time.perf_counter() - t0
+    dkm = type("Km", (), {k: dev(getattr(km, k)) for k in ("s", "K", "bk_a", "bk_e", "ksk_a", "ksk_e")})
+    bk = torch.zeros(vp.BK_WORDS, dtype=torch.int32, device="cuda")
+    ksk = torch.zeros(vp.KSK_WORDS, dtype=torch.int32, device="cuda")
+    vp.velopir_gpu_keygen(ctx, dkm, bk, ksk)        # warm
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        vp.velopir_gpu_keygen(ctx, dkm, bk, ksk)
+        ts.append(time.perf_counter() - t0)
+    same = bool(np.array_equal(bk.cpu().numpy().view(np.uint32), bk_h) and
+                np.array_equal(ksk.cpu().numpy().view(np.uint32), ksk_h))
+    res = [{"workload": "cloud key (BK + KSK)", "host_client_s": t_host, "gpu_s": float(min(ts)),
+            "speedup": t_host / min(ts), "correct": same}]
+    # 32,768 encryptions of zero, with the key-switching key's masks and noises as material
+    a = np.ascontiguousarray(km.ksk_a.reshape(-1, 630), dtype=np.uint32)
+    e = np.ascontiguousarray(km.ksk_e.reshape(-1), dtype=np.uint32)
+    lm = synth.LweMaterial(a, e)
+    t0 = time.perf_counter()
+    pk_h = vp.velopir_client_pubkeygen(s, lm)
+    t_host = time.perf_counter() - t0
+    da, de, ds = dev(a), dev(e), dev(s)
+    pk = torch.zeros((e.size, 631), dtype=torch.int32, device="cuda")
+    vp.velopir_gpu_pubkeygen(ctx, ds, da, de, pk)   # warm
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        vp.velopir_gpu_pubkeygen(ctx, ds, da, de, pk)
+        ts.append(time.perf_counter() - t0)
+    res.append({"workload": f"Alg. PubKeyGen, {e.size} encryptions of zero", "host_client_s": t_host,
+                "gpu_s": float(min(ts)), "speedup": t_host / min(ts),
+                "correct": bool(np.array_equal(pk.cpu().numpy().view(np.uint32), pk_h))})
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--which", default="idm8,idm32,cov64")
@@ -253,7 +302,7 @@ def main():
     vp.velopir_load_cloud_key(ctx.h, bk, ksk)
     vp.velopir_autotune(ctx.h)
     runs = {"idm8": run_idm8, "idm32": run_idm32, "cov64": run_cov64, "intv_encdb": run_intv_encdb,
-            "paper4": run_paper4}
+            "paper4": run_paper4, "client": run_client}
     ok = True
     for name in args.which.split(","):
         res = runs[name](ctx.h, km.s)

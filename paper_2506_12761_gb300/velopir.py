@@ -43,6 +43,7 @@ EXPORTS = [
     "velopir_interval_query_encdb", "velopir_coordinate_query_encdb", "velopir_id_match_encdb", "velopir_cancel",
     "velopir_plan_batch", "velopir_trace_start", "velopir_trace_stop", "velopir_set_launch_limit",
     "velopir_serve_start", "velopir_serve_stop", "velopir_set_encdb_fanin",
+    "velopir_gpu_keygen", "velopir_gpu_encrypt_bits", "velopir_gpu_pubkeygen", "velopir_gpu_server_encrypt",
 ]
 # Every symbol include/velopir_client.h declares (the host-only client library).
 CLIENT_EXPORTS = [
@@ -154,6 +155,10 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_double)]),
             "velopir_trace_start": (i, [vp, u64, ctypes.c_uint32, ctypes.c_uint32, sz]),
             "velopir_trace_stop": (i, [vp, vp, sz, ctypes.POINTER(sz)]),
+            "velopir_gpu_keygen": (i, [vp, ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp, vp]),
+            "velopir_gpu_encrypt_bits": (i, [vp, vp, vp, vp, vp, sz, vp]),
+            "velopir_gpu_pubkeygen": (i, [vp, vp, vp, vp, sz, vp]),
+            "velopir_gpu_server_encrypt": (i, [vp, vp, vp, sz, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -382,6 +387,41 @@ def velopir_client_decrypt_bits(s, ct) -> np.ndarray:
     _check_client(clib().velopir_client_decrypt_bits(ptr(np.ascontiguousarray(s, dtype=np.uint32)), ptr(ct),
                                                    ct.shape[0], ptr(out)))
     return out
+
+
+def _u32c(x):
+    """numpy arrays as contiguous uint32; torch tensors pass through (they must be contiguous 32-bit)."""
+    return np.ascontiguousarray(x, dtype=np.uint32) if isinstance(x, np.ndarray) else x
+
+
+def velopir_gpu_keygen(ctx, km, bk_out, ksk_out, params: Params | None = None) -> None:
+    """Cloud key on the GPU from synth.KeyMaterial-like fields (numpy arrays or
+    torch tensors, host or device) into bk_out / ksk_out (host or device)."""
+    p = params or paper_params()
+    c = {k: _u32c(getattr(km, k)) for k in ("s", "K", "bk_a", "bk_e", "ksk_a", "ksk_e")}
+    _check(ctx, lib().velopir_gpu_keygen(ctx, ctypes.byref(p), ptr(c["s"]), ptr(c["K"]), ptr(c["bk_a"]),
+                                         ptr(c["bk_e"]), ptr(c["ksk_a"]), ptr(c["ksk_e"]), ptr(bk_out), ptr(ksk_out)))
+
+
+def velopir_gpu_encrypt_bits(ctx, s, bits, a, e, out) -> None:
+    """Section 2.2 Enc of len(bits) bits on the GPU into out[count][631] (host or device buffers)."""
+    bits, a, e, s = _u32c(bits), _u32c(a), _u32c(e), _u32c(s)
+    count = int(np.prod(bits.shape))
+    _check(ctx, lib().velopir_gpu_encrypt_bits(ctx, ptr(s), ptr(bits), ptr(a), ptr(e), count, ptr(out)))
+
+
+def velopir_gpu_pubkeygen(ctx, s, a, e, out) -> None:
+    """Alg. PubKeyGen on the GPU: encryptions of zero, one per noise word of e."""
+    a, e, s = _u32c(a), _u32c(e), _u32c(s)
+    count = int(np.prod(e.shape))
+    _check(ctx, lib().velopir_gpu_pubkeygen(ctx, ptr(s), ptr(a), ptr(e), count, ptr(out)))
+
+
+def velopir_gpu_server_encrypt(ctx, pk, bits, out) -> None:
+    """Alg. ServerEnc on the GPU: (0, Ecd(bit)) + pk, one ciphertext per bit."""
+    pk, bits = _u32c(pk), _u32c(bits)
+    count = int(np.prod(bits.shape))
+    _check(ctx, lib().velopir_gpu_server_encrypt(ctx, ptr(pk), ptr(bits), count, ptr(out)))
 
 
 class Context:

@@ -89,6 +89,12 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.velopir_bootstrap_batch(None, 0, None, None, 1) == -1
     assert lib.velopir_sync(None) == -1
     assert lib.velopir_destroy(None) == 0
+    # the client preprocessing on the GPU checks its context before any CUDA call
+    p = vp.paper_params()
+    assert lib.velopir_gpu_keygen(None, ctypes.byref(p), None, None, None, None, None, None, None, None) == -1
+    assert lib.velopir_gpu_encrypt_bits(None, None, None, None, None, 1, None) == -1
+    assert lib.velopir_gpu_pubkeygen(None, None, None, None, 1, None) == -1
+    assert lib.velopir_gpu_server_encrypt(None, None, None, 1, None) == -1
 
 
 def test_client_keygen_matches_oracle(lib, paper_keys):

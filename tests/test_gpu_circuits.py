@@ -23,16 +23,30 @@ def test_idm8_d4_whole_circuit(paper_keys):
     assert list(vp.velopir_client_decrypt_bits(s, out)) == [int(i == w["query"]) for i in ids]
 
 
+_INTV = {}
+
+
+def _intv_small(paper_keys, s):
+    """Three rectangles (the first contains the point) and the oracle's whole
+    IntV circuit on them, computed once for the tests that share them."""
+    if not _INTV:
+        w = synth.intv_workload(3, substream=1)
+        rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
+        rects[0] = [max(0, w["x"] - 5), w["x"] + 5, max(0, w["y"] - 9), w["y"] + 1]
+        cx = encrypt_value_bits(s, w["x"], 32, 501)
+        cy = encrypt_value_bits(s, w["y"], 32, 502)
+        _INTV.update(w=w, rects=rects, cx=cx, cy=cy,
+                     want=oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
+    return _INTV
+
+
 def test_intv_small_whole_circuit(paper_keys):
     ctx, s = gpu_ctx()
-    w = synth.intv_workload(3, substream=1)
-    rects = w["rects"].copy()
-    rects[0] = [max(0, w["x"] - 5), w["x"] + 5, max(0, w["y"] - 9), w["y"] + 1]  # contains the point
-    cx = encrypt_value_bits(s, w["x"], 32, 501)
-    cy = encrypt_value_bits(s, w["y"], 32, 502)
+    c = _intv_small(paper_keys, s)
+    w, rects = c["w"], c["rects"]
     out = np.zeros((3, 631), dtype=np.uint32)
-    vp.velopir_interval_query(ctx.h, cx, cy, rects, 3, out)
-    assert np.array_equal(out, oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
+    vp.velopir_interval_query(ctx.h, c["cx"], c["cy"], rects, 3, out)
+    assert np.array_equal(out, c["want"])
     want = [int(r[0] <= w["x"] < r[1] and r[2] <= w["y"] < r[3]) for r in rects.astype(np.int64)]
     assert list(vp.velopir_client_decrypt_bits(s, out)) == want and want[0] == 1
 
@@ -78,19 +92,17 @@ def test_degenerate_shapes(paper_keys):
 
 
 def test_device_resident_database(paper_keys):
-    """Ciphertexts, database and output all in device memory."""
+    """Ciphertexts, database and output all in device memory (the workload of
+    test_intv_small_whole_circuit, checked against the same oracle run)."""
     import torch
     ctx, s = gpu_ctx()
-    w = synth.intv_workload(2, substream=4)
-    cx = encrypt_value_bits(s, w["x"], 32, 507)
-    cy = encrypt_value_bits(s, w["y"], 32, 508)
-    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
-    dx, dy = (torch.from_numpy(a.view(np.int32)).cuda() for a in (cx, cy))
-    dr = torch.from_numpy(rects.view(np.int32)).cuda()
-    dout = torch.zeros((2, 631), dtype=torch.int32, device="cuda")
-    vp.velopir_interval_query(ctx.h, dx, dy, dr, 2, dout)
+    c = _intv_small(paper_keys, s)
+    dx, dy = (torch.from_numpy(a.view(np.int32)).cuda() for a in (c["cx"], c["cy"]))
+    dr = torch.from_numpy(c["rects"].view(np.int32)).cuda()
+    dout = torch.zeros((3, 631), dtype=torch.int32, device="cuda")
+    vp.velopir_interval_query(ctx.h, dx, dy, dr, 3, dout)
     out = dout.cpu().numpy().view(np.uint32)
-    assert np.array_equal(out, oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
+    assert np.array_equal(out, c["want"])
 
 
 def test_launch_limit_one_is_one_bootstrap_per_launch(paper_keys):
