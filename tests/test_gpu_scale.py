@@ -49,7 +49,7 @@ def test_idm32_d8192_match_bits_and_pairwise_aggregation_traced(paper_keys):
     sample = sorted({0, 1, 4097, D - 1, w["planted"]})
     assert np.array_equal(match[sample], oracle.idm_batch(paper_keys, x, ids[sample]))
 
-    vp.velopir_trace_start(ctx.h, TRACE_SEED, 32, 100, 8192)
+    vp.velopir_trace_start(ctx.h, TRACE_SEED, 32, 125, 8192)      # >= 516,064 / 125 = 4,129 gates
     agg = np.zeros((32, 631), dtype=np.uint32)
     vp.velopir_id_match(ctx.h, x, 32, ids, D, pay, 32, agg)
     recs = vp.velopir_trace_stop(ctx.h, 8192)
@@ -117,7 +117,7 @@ def test_cov_12_uneven_queries_one_graph_traced(paper_keys):
         out = np.zeros((int(D), 631), dtype=np.uint32)
         qs.append((w, cell, cells, out))
         recs_q.append(vp.make_query(vp.VP_QUERY_COV, cell, cells, int(D), out))
-    vp.velopir_trace_start(ctx.h, TRACE_SEED + 2, 8, 256, 16384)
+    vp.velopir_trace_start(ctx.h, TRACE_SEED + 2, 8, 270, 16384)   # >= 1,137,793 / 270 = 4,215 gates
     vp.velopir_query_batch(ctx.h, recs_q, use_graph=True)
     recs = vp.velopir_trace_stop(ctx.h, 16384)
     assert len(recs) < 16384

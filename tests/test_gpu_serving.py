@@ -256,3 +256,54 @@ def test_issue_thread_serves_staggered_arrivals(paper_keys):
     for q in qs:
         assert np.array_equal(q["out"], oracle_out(paper_keys, q))
     assert vp.velopir_queue_depth(ctx.h) == (0, 0)
+
+
+def test_serving_mix_traced_at_scale(paper_keys):
+    """The serving workload's 40/30/30 IntV/CoV/IdM mix at sizes a test can
+    afford (IntV D = 256 and 128; CoV D = 1,024 and 512; IdM-32 D = 2,048
+    and 1,024 with payloads aggregated by fan-in 8: 207,232 bootstraps),
+    arriving one every few serving steps while the others run.  Of every
+    serving step's launches a seeded sample of >= 4,096 gates in all is
+    recomputed by the oracle from the recorded inputs (bit-identical), and
+    every output decrypts to its plaintext answer."""
+    ctx, s = gpu_ctx()
+    vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
+    qs, answers = [], []
+    for k, D in enumerate((256, 128)):
+        w = synth.intv_workload(D, substream=60 + k)
+        cx = encrypt_value_bits(s, w["x"], 32, 960 + 2 * k)
+        cy = encrypt_value_bits(s, w["y"], 32, 961 + 2 * k)
+        r = np.ascontiguousarray(w["rects"], dtype=np.uint32)
+        qs.append(dict(kind=vp.VP_QUERY_INTV, a=cx, b=cy, db=r, D=D, out=np.zeros((D, 631), np.uint32)))
+        r64 = r.astype(np.int64)
+        answers.append(((r64[:, 0] <= w["x"]) & (w["x"] < r64[:, 1]) & (r64[:, 2] <= w["y"]) &
+                        (w["y"] < r64[:, 3])).astype(np.uint32))
+    for k, D in enumerate((1024, 512)):
+        w = synth.cov_workload(D, substream=62 + k)
+        cell = encrypt_value_bits(s, w["cell"], 32, 964 + k)
+        cells = w["cells"].astype(np.uint32)
+        qs.append(dict(kind=vp.VP_QUERY_COV, a=cell, db=cells, D=D, out=np.zeros((D, 631), np.uint32)))
+        answers.append((cells == w["cell"]).astype(np.uint32))
+    for k, D in enumerate((2048, 1024)):
+        w = synth.idm_workload(D, 32, distinct=True, payload=True, substream=64 + k)
+        x = encrypt_value_bits(s, w["query"], 32, 966 + k)
+        pay = w["payload"].astype(np.uint32)
+        qs.append(dict(kind=vp.VP_QUERY_IDM, a=x, db=w["ids"].astype(np.uint32), D=D, id_bits=32, payload=pay,
+                       payload_bits=32, out=np.zeros((32, 631), np.uint32), fanin=8))
+        answers.append(np.array([(int(pay[w["planted"]]) >> j) & 1 for j in range(32)], dtype=np.uint32))
+    vp.velopir_trace_start(ctx.h, 35, 16, 48, 8192)      # >= 207,232 / 48 = 4,318 gates
+    order = [0, 2, 4, 1, 3, 5]          # arrivals alternate between the modes
+    tickets, seen, steps, nxt = {}, set(), 0, 0
+    while len(seen) < len(qs):
+        if nxt < len(order) and steps % 3 == 0:
+            tickets[vp.velopir_submit(ctx.h, as_record(qs[order[nxt]]))] = order[nxt]
+            nxt += 1
+        seen.update(vp.velopir_progress(ctx.h))
+        steps += 1
+        assert steps < 5000
+    recs = vp.velopir_trace_stop(ctx.h, 8192)
+    assert seen == set(tickets) and vp.velopir_queue_depth(ctx.h) == (0, 0)
+    assert len(recs) < 8192, "the trace buffer filled up: later steps were not sampled"
+    for q, want in zip(qs, answers):
+        assert np.array_equal(vp.velopir_client_decrypt_bits(s, q["out"]), want), q["kind"]
+    check_trace(paper_keys, recs, 4096)
