@@ -3,7 +3,9 @@
  * GB300 (sm_103a) and the server-side circuits of VeLoPIR's three query modes.
  * Key generation, encryption, decryption and Alg. PubKeyGen / ServerEnc are
  * in the separate host-only library libvelopir_client.so (velopir_client.h),
- * which needs no GPU and no CUDA runtime.
+ * which needs no GPU and no CUDA runtime; the same computations also run here
+ * as CUDA kernels (velopir_gpu_*), bit-identical, for a key that should stay
+ * on the device and for Alg. ServerEnc over a large database.
  *
  * Paper: "Versatile and Fast Location-Based PIR with FHE over the Torus"
  * (VeLoPIR).  Section 2.2 defines TLWE encryption, Ecd, Dec and the gate
