@@ -186,10 +186,12 @@ def cpu_oracle_config1():
             "workload": "identifier matching, 8-bit encrypted id vs D=4 plaintext ids (28 bootstraps), whole circuit"}
 
 
-def bench_config(world: int, sample: str) -> dict:
-    """The `config` record of both arms: the same keys, the workload and what each arm timed."""
+def bench_config(world: int) -> dict:
+    """The `config` record, identical in both arms (what each arm timed of the
+    workload is stated beside it, under "run")."""
     return {"workload": WORKLOAD, "D": D, "bootstraps_per_step": BOOTSTRAPS_PER_STEP,
-            "parallelism": f"replicas x{world}", "sample": sample}
+            "parallelism": f"replicas x{world}",
+            "l2": "GPU arm: L2 flushed between timed steps (256 MiB write, untimed); the CPU arm has no GPU cache"}
 
 
 def run_reference(args):
@@ -211,7 +213,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": BOOTSTRAPS_PER_STEP / v * 1e3,
             "ms_per_step_basis": "extrapolated from the timed sample (a full CPU query takes about an hour)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": bench_config(world, sample),
+            "config": bench_config(world), "run": {"sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle", "sample": info[1],
                              "config1_full_circuit": c1},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -446,10 +448,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": bench_config(world, "each step: the whole query, every bootstrap of it"),
-                "run": {"path": args.path,
-                        "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves))},
-                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
+                "config": bench_config(world),
+                "run": {"sample": "each step: the whole query, every bootstrap of it", "path": args.path,
+                        "tile_shapes": {"wave_ms_by_bootstraps_per_cta": dict(zip(vp.NTT_TILE_SHAPES, waves))}},
                 "query_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
                 "plain": {"value": plain_rate, "unit": UNIT, "repeats": [float(x) for x in plain_rates],
                           "note": "one bootstrap per kernel launch, same kernels; median of 3 passes after a warm-up"},
