@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import encrypt_value_bits, gpu_ctx
+from gpu_common import encrypt_value_bits, gpu_ctx, make_queries, oracle_out
 from paper_2506_12761_gb300 import synth
 from paper_2506_12761_gb300 import velopir as vp
 
@@ -23,29 +23,20 @@ def test_idm8_d4_whole_circuit(paper_keys):
     assert list(vp.velopir_client_decrypt_bits(s, out)) == [int(i == w["query"]) for i in ids]
 
 
-_INTV = {}
-
-
 def _intv_small(paper_keys, s):
-    """Three rectangles (the first contains the point) and the oracle's whole
-    IntV circuit on them, computed once for the tests that share them."""
-    if not _INTV:
-        w = synth.intv_workload(3, substream=1)
-        rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
-        rects[0] = [max(0, w["x"] - 5), w["x"] + 5, max(0, w["y"] - 9), w["y"] + 1]
-        cx = encrypt_value_bits(s, w["x"], 32, 501)
-        cy = encrypt_value_bits(s, w["y"], 32, 502)
-        _INTV.update(w=w, rects=rects, cx=cx, cy=cy,
-                     want=oracle.intv_batch(paper_keys, cx, cy, rects.astype(np.uint64)))
-    return _INTV
+    """The serving tests' two-rectangle IntV query (the first rectangle
+    contains the point) and the oracle's whole circuit on it, from the shared
+    oracle runs."""
+    q = make_queries(s, 3)[0]
+    return dict(w=q["w"], rects=q["db"], cx=q["a"], cy=q["b"], D=q["D"], want=oracle_out(paper_keys, q))
 
 
 def test_intv_small_whole_circuit(paper_keys):
     ctx, s = gpu_ctx()
     c = _intv_small(paper_keys, s)
     w, rects = c["w"], c["rects"]
-    out = np.zeros((3, 631), dtype=np.uint32)
-    vp.velopir_interval_query(ctx.h, c["cx"], c["cy"], rects, 3, out)
+    out = np.zeros((c["D"], 631), dtype=np.uint32)
+    vp.velopir_interval_query(ctx.h, c["cx"], c["cy"], rects, c["D"], out)
     assert np.array_equal(out, c["want"])
     want = [int(r[0] <= w["x"] < r[1] and r[2] <= w["y"] < r[3]) for r in rects.astype(np.int64)]
     assert list(vp.velopir_client_decrypt_bits(s, out)) == want and want[0] == 1
@@ -99,8 +90,8 @@ def test_device_resident_database(paper_keys):
     c = _intv_small(paper_keys, s)
     dx, dy = (torch.from_numpy(a.view(np.int32)).cuda() for a in (c["cx"], c["cy"]))
     dr = torch.from_numpy(c["rects"].view(np.int32)).cuda()
-    dout = torch.zeros((3, 631), dtype=torch.int32, device="cuda")
-    vp.velopir_interval_query(ctx.h, dx, dy, dr, 3, dout)
+    dout = torch.zeros((c["D"], 631), dtype=torch.int32, device="cuda")
+    vp.velopir_interval_query(ctx.h, dx, dy, dr, c["D"], dout)
     out = dout.cpu().numpy().view(np.uint32)
     assert np.array_equal(out, c["want"])
 

@@ -9,9 +9,7 @@ and decrypts every output."""
 import numpy as np
 import pytest
 
-import oracle
-from gpu_common import encrypt_value_bits, gpu_ctx
-from paper_2506_12761_gb300 import synth
+from gpu_common import fullsize_inputs, fullsize_oracle, gpu_ctx
 from paper_2506_12761_gb300 import velopir as vp
 
 pytestmark = pytest.mark.gpu
@@ -22,16 +20,9 @@ def test_intv_d1024_full_size(paper_keys):
     ctx, s = gpu_ctx()
     vp.velopir_set_path(ctx.h, vp.VP_PATH_NTT)
     vp.velopir_autotune(ctx.h)
-    D = 1024
-    w = synth.intv_workload(D)
-    cx = vp.velopir_client_encrypt_bits(s, synth.value_bits([w["x"]], 32)[0], synth.lwe_material(32, substream=1))
-    cy = vp.velopir_client_encrypt_bits(s, synth.value_bits([w["y"]], 32)[0], synth.lwe_material(32, substream=2))
-    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
-    out = np.zeros((D, 631), dtype=np.uint32)
-    vp.velopir_interval_query(ctx.h, cx, cy, rects, D, out)
-    r = rects.astype(np.int64)
-    want = ((r[:, 0] <= w["x"]) & (w["x"] < r[:, 1]) & (r[:, 2] <= w["y"]) & (w["y"] < r[:, 3])).astype(np.uint32)
-    assert np.array_equal(vp.velopir_client_decrypt_bits(s, out), want)
-    sample = sorted({0, 1, D // 2, D - 1} | set(np.flatnonzero(want)[:2].tolist()))
-    got = oracle.intv_batch(paper_keys, cx, cy, rects[sample].astype(np.uint64))
-    assert np.array_equal(out[sample], got)
+    f = fullsize_inputs(s)
+    out = np.zeros((f["D"], 631), dtype=np.uint32)
+    vp.velopir_interval_query(ctx.h, f["cx"], f["cy"], f["rects"], f["D"], out)
+    assert np.array_equal(vp.velopir_client_decrypt_bits(s, out), f["want"])
+    assert f["want"].sum() >= 1
+    assert np.array_equal(out[f["sample"]], fullsize_oracle(paper_keys))

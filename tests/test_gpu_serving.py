@@ -5,66 +5,11 @@ alone."""
 import numpy as np
 import pytest
 
-import oracle
-from gpu_common import check_trace, encrypt_value_bits, gpu_ctx
+from gpu_common import as_record, check_trace, encrypt_value_bits, gpu_ctx, make_queries, oracle_out
 from paper_2506_12761_gb300 import synth
 from paper_2506_12761_gb300 import velopir as vp
 
 pytestmark = pytest.mark.gpu
-
-
-def make_queries(s, seed, fanin=0):
-    """IntV D=2, CoV D=3, IdM-8 D=4 with payload (aggregated pairwise, or with
-    fan-in `fanin`): three modes, uneven sizes."""
-    qs = []
-    w = synth.intv_workload(2, substream=seed)
-    cx, cy = encrypt_value_bits(s, w["x"], 32, 900 + seed), encrypt_value_bits(s, w["y"], 32, 901 + seed)
-    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
-    qs.append(dict(kind=vp.VP_QUERY_INTV, a=cx, b=cy, db=rects, D=2, out=np.zeros((2, 631), np.uint32)))
-    w = synth.cov_workload(3, substream=seed + 1)
-    cell = encrypt_value_bits(s, w["cell"], 32, 902 + seed)
-    qs.append(dict(kind=vp.VP_QUERY_COV, a=cell, db=w["cells"].astype(np.uint32), D=3, out=np.zeros((3, 631), np.uint32)))
-    w = synth.idm_workload(4, 8, payload=True, substream=seed + 2)
-    x = encrypt_value_bits(s, w["query"], 8, 903 + seed)
-    qs.append(dict(kind=vp.VP_QUERY_IDM, a=x, db=w["ids"].astype(np.uint32), D=4, id_bits=8,
-                   payload=w["payload"].astype(np.uint32), payload_bits=32, out=np.zeros((32, 631), np.uint32),
-                   fanin=fanin))
-    return qs
-
-
-def as_record(q):
-    return vp.make_query(q["kind"], q["a"], q["db"], q["D"], q["out"], enc_b=q.get("b"), id_bits=q.get("id_bits", 0),
-                         payload=q.get("payload"), payload_bits=q.get("payload_bits", 0), agg_fanin=q.get("fanin", 0))
-
-
-def _oracle_circuit(keys, q):
-    if q["kind"] == vp.VP_QUERY_INTV:
-        return oracle.intv_batch(keys, q["a"], q["b"], q["db"].astype(np.uint64))
-    if q["kind"] == vp.VP_QUERY_COV:
-        return oracle.cov_batch(keys, q["a"], q["db"])
-    return oracle.idm_payload(keys, q["a"], q["db"], q["payload"], q["payload_bits"], fanin=max(2, q.get("fanin", 0)))
-
-
-_ORACLE = {}
-
-
-def oracle_out(keys, q):
-    """The oracle's circuit for one query, from the query's own ciphertexts.
-    The serving tests share two query sets (make_queries seeds 3 and 4); their
-    oracle outputs are computed once, all six circuits at a time."""
-    key = (q["kind"], q["a"].tobytes(), q.get("fanin", 0))
-    if key not in _ORACLE:
-        from concurrent.futures import ThreadPoolExecutor
-        _, s = gpu_ctx()
-        todo = [x for x in make_queries(s, 3) + make_queries(s, 4, fanin=4)
-                if (x["kind"], x["a"].tobytes(), x.get("fanin", 0)) not in _ORACLE]
-        if not any((x["kind"], x["a"].tobytes(), x.get("fanin", 0)) == key for x in todo):
-            todo.append(q)
-        with ThreadPoolExecutor(len(todo)) as ex:
-            outs = list(ex.map(lambda x: _oracle_circuit(keys, x), todo))
-        for x, o in zip(todo, outs):
-            _ORACLE[(x["kind"], x["a"].tobytes(), x.get("fanin", 0))] = o
-    return _ORACLE[key]
 
 
 def run_alone(ctx, q):
