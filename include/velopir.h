@@ -472,7 +472,9 @@ typedef struct {
  * to velopir_load_cloud_key, and a server can run Alg. ServerEnc over a large
  * database on the device that evaluates it.  Every buffer may be host or
  * device memory; host buffers are staged through stream-ordered temporaries
- * released before the call returns.  The context's key need not be loaded.
+ * (cudaMallocAsync) released before the call returns and not counted against
+ * the context's HBM budget -- pass device buffers to avoid them.  The
+ * context's key need not be loaded.
  * Synchronous.  Errors: ERR_ARG (null buffer, other parameters, count above
  * 2^24), ERR_OOM (staging), ERR_CUDA, ERR_BUSY (the issue thread runs). */
 
