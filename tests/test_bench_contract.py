@@ -40,3 +40,29 @@ def test_reference_and_gpu_arms_share_metric_unit_and_config(reference_line):
     assert reference_line["metric"] == bench.METRIC and reference_line["unit"] == bench.UNIT
     assert reference_line["config"] == bench.bench_config(1)
     assert reference_line["config"]["workload"] and "l2" in reference_line["config"]
+
+
+def test_bench_query_schedule_on_the_host():
+    """The benchmark's step (IntV, D = 1,024) as the scheduler issues it, by
+    the host dry run: 134,144 blind rotations, the plaintext answer, and the
+    wave-filled plan of 36 launches of two full 12-wide waves, one of one
+    wave and a 992-gate tail -- 74 waves, where its 34 as-soon-as-possible
+    layers would take 99."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2506_12761_gb300 import synth
+    from paper_2506_12761_gb300 import velopir as vp
+    w = synth.intv_workload(bench.D)
+    rects = np.ascontiguousarray(w["rects"], dtype=np.uint32)
+    bits = lambda v: np.array([(int(v) >> i) & 1 for i in range(32)], dtype=np.uint32)
+    wave = 152 * 12
+    out, sizes = vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, bench.D, bits(w["x"]), bits(w["y"]), wave=wave)
+    r = rects.astype(np.int64)
+    want = ((r[:, 0] <= w["x"]) & (w["x"] < r[:, 1]) & (r[:, 2] <= w["y"]) & (w["y"] < r[:, 3])).astype(np.uint32)
+    assert np.array_equal(out, want)
+    assert sum(sizes) == bench.BOOTSTRAPS_PER_STEP == 134144
+    assert sorted(sizes) == [992, 1824] + [2 * wave] * 36
+    _, layers = vp.velopir_plan_query(vp.VP_QUERY_INTV, rects, bench.D, bits(w["x"]), bits(w["y"]), wave=0)
+    assert len(layers) == 34
+    assert sum(-(-s // wave) for s in layers) == 99 and sum(-(-s // wave) for s in sizes) == 74
