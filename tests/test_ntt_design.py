@@ -43,10 +43,14 @@ def tables(p):
 TW = {p: tables(p) for p in P}
 
 
+SHOUP_COUNT = [0]   # Shoup products executed, for the work count of the roofline
+
+
 def shoup(x, w, p):
     """x * w mod p in [0, 2p) with ws = floor(w 2^32 / p); x < 2^32 required."""
     x = np.asarray(x, dtype=np.uint64)
     w = np.asarray(w, dtype=np.uint64)
+    SHOUP_COUNT[0] += int(np.broadcast(x, w).size)
     assert int(x.max()) <= M32
     ws = (w << np.uint64(32)) // np.uint64(p)
     q = (x * ws) >> np.uint64(32)
@@ -135,8 +139,10 @@ def key_hat(bk_row, p):
     return (k % np.uint64(p)) * np.uint64(ninv) % np.uint64(p)
 
 
-def external_product(digits, bk):
+def external_product(digits, bk, khat=None):
     """digits int64[6][N] in [-64, 63], bk uint32[6][2][N]: out uint32[2][N] as the kernel computes it."""
+    if khat is None:
+        khat = {(p, r, j): key_hat(bk[r][j], p) for p in P for r in range(6) for j in range(2)}
     res = {}
     for p in P:
         acc = [np.zeros(N, dtype=np.uint64) for _ in range(2)]
@@ -144,7 +150,7 @@ def external_product(digits, bk):
             x = forward(digit_stages_by_lookup(digits[r], p), p, s0=2, bound=6 * p)
             assert int(x.max()) < 22 * p
             for j in range(2):
-                acc[j] = acc[j] + shoup(x, key_hat(bk[r][j], p), p)
+                acc[j] = acc[j] + shoup(x, khat[(p, r, j)], p)
                 assert int(acc[j].max()) < 12 * p
         res[p] = [inverse2(red_shoup(acc[j], p), p) for j in range(2)]
     p0, p1 = P
@@ -202,3 +208,20 @@ def test_mixed_signs_and_ragged_digits():
     bk[:, 1, ::3] = 0
     bk[2, 0, ::5] = 1
     assert np.array_equal(external_product(d, bk), exact(d, bk))
+
+
+def test_executed_work_matches_the_roofline_count():
+    """The Shoup products one external product executes (8 multiplying
+    stages of 12 forward digit transforms, the pointwise products, 4 inverse
+    transforms and the CRT lift) equal the per-step count behind the
+    benchmark's roofline (ntt_model), and the lookups replace exactly the
+    first two stages."""
+    from paper_2506_12761_gb300 import ntt_model
+    rng = np.random.default_rng(11)
+    d = rng.integers(-64, 64, size=(6, N), dtype=np.int64)
+    bk = rng.integers(0, 1 << 32, size=(6, 2, N), dtype=np.uint64).astype(np.uint32)
+    khat = {(p, r, j): key_hat(bk[r][j], p) for p in P for r in range(6) for j in range(2)}
+    SHOUP_COUNT[0] = 0
+    external_product(d, bk, khat)
+    assert SHOUP_COUNT[0] == ntt_model.SHOUP_PER_STEP == 12 * 8 * 512 + 2 * 6 * 2 * N + 4 * 10 * 512 + 2 * N
+    assert ntt_model.IMAD_SLOTS_PER_BOOTSTRAP == (4 * ntt_model.SHOUP_PER_STEP + ntt_model.CRT_PER_STEP) * 630
